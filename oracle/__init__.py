@@ -1,0 +1,238 @@
+"""FP64 CPU oracle for the parabolic operators and integrators of arXiv:1610.01265.
+
+TEST INFRASTRUCTURE ONLY: imported by the tests, by the smoke check and by the
+benchmark's CPU-baseline leg, never by the product path.  The arithmetic lives in
+``oracle.c`` (plain loops, written from the paper); this module only compiles it
+(gcc, in-tree under ``oracle/_build``) and marshals numpy arrays through ctypes.
+
+Layout: scalar fields are float64 arrays of shape (nph, nth, nr) (r fastest);
+operators are full 19-slot rows, shape (N, 19), slot s = neighbour at offsets()[s].
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+NSLOT = 19
+PC_JACOBI = 1
+PC_BILU0 = 2
+STATUS = {0: "converged", 1: "not converged", 2: "breakdown", -1: "bad arguments"}
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into oracle/_build/liboracle.so (OpenMP when gcc supports it)."""
+    src = os.path.join(_HERE, "oracle.c")
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(src):
+        return _LIB_PATH
+    os.makedirs(_BUILD, exist_ok=True)
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    base = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", src, "-o", tmp, "-lm"]
+    try:
+        subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True, capture_output=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB_PATH)
+            D = ctypes.c_double
+            P = ctypes.c_void_p
+            I = ctypes.c_int
+            lib.or_assemble_conduction.argtypes = [I, I, I, P, P, P, P, D, I, P, P]
+            lib.or_assemble_viscosity.argtypes = [I, I, I, P, P, P, P, P]
+            lib.or_energy_conduction.argtypes = [I, I, I, P, P, P, P, D, I, P]
+            lib.or_energy_conduction.restype = D
+            lib.or_apply_F.argtypes = [I, I, I, P, P, P, P, P]
+            lib.or_gershgorin_dt.argtypes = [I, I, I, P, P, P, P]
+            lib.or_gershgorin_dt.restype = D
+            lib.or_rkl2_stages.argtypes = [D, I]
+            lib.or_rkl2_coeffs.argtypes = [I, P, P, P, P]
+            lib.or_rkl2_superstep.argtypes = [I, I, I, P, P, P, P, D, I]
+            lib.or_bilu0_factor.argtypes = [I, I, I, P, P, P, P]
+            lib.or_bilu0_apply.argtypes = [I, I, I, P, P, P, P, P]
+            lib.or_be_pcg.argtypes = [I, I, I, P, P, P, P, D, I, P, D, I, P, I, P, P]
+            lib.or_offsets.argtypes = [P]
+            lib.or_num_threads.restype = I
+            _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class Grid:
+    """nr x nth x nph cell-centred spherical grid; rf = nr+1 radial faces in R_sun."""
+
+    def __init__(self, rf, nth: int, nph: int):
+        self.rf = _f64(rf)
+        self.nr = len(self.rf) - 1
+        self.nth = int(nth)
+        self.nph = int(nph)
+
+    @property
+    def shape(self):
+        return (self.nph, self.nth, self.nr)
+
+    @property
+    def N(self):
+        return self.nr * self.nth * self.nph
+
+    def _dims(self):
+        return (self.nr, self.nth, self.nph, _ptr(self.rf))
+
+
+def offsets() -> np.ndarray:
+    out = np.zeros((NSLOT, 3), dtype=np.int32)
+    _load().or_offsets(_ptr(out))
+    return out
+
+
+def num_threads() -> int:
+    return _load().or_num_threads()
+
+
+def assemble_conduction(g: Grid, T, bhat, n, kappa0: float = 9e-7, beta_tcut: bool = False,
+                        isotropic: bool = False):
+    """S (N,19) = Hessian of the discrete energy, W (N,) = 3 k_B n V."""
+    T, bhat, n = _f64(T), _f64(bhat), _f64(n)
+    S = np.empty((g.N, NSLOT))
+    W = np.empty(g.N)
+    flags = (1 if beta_tcut else 0) | (2 if isotropic else 0)
+    rc = _load().or_assemble_conduction(*g._dims(), _ptr(T), _ptr(bhat), _ptr(n), kappa0, flags,
+                                        _ptr(S), _ptr(W))
+    if rc != 0:
+        raise ValueError("bad grid for the oracle (needs nr>=1, nth>=1, nph>=3)")
+    return S, W
+
+
+def assemble_viscosity(g: Grid, rho, nu):
+    rho, nu = _f64(rho), _f64(nu)
+    S = np.empty((g.N, NSLOT))
+    W = np.empty(g.N)
+    rc = _load().or_assemble_viscosity(*g._dims(), _ptr(rho), _ptr(nu), _ptr(S), _ptr(W))
+    if rc != 0:
+        raise ValueError("bad grid for the oracle")
+    return S, W
+
+
+def energy_conduction(g: Grid, T, bhat, n, u, kappa0: float = 9e-7, beta_tcut: bool = False,
+                      isotropic: bool = False) -> float:
+    T, bhat, n, u = _f64(T), _f64(bhat), _f64(n), _f64(u)
+    flags = (1 if beta_tcut else 0) | (2 if isotropic else 0)
+    return _load().or_energy_conduction(*g._dims(), _ptr(T), _ptr(bhat), _ptr(n), kappa0, flags,
+                                        _ptr(u))
+
+
+def apply_F(g: Grid, S, W, u) -> np.ndarray:
+    S, W, u = _f64(S), _f64(W), _f64(u)
+    out = np.empty(g.N)
+    _load().or_apply_F(*g._dims(), _ptr(S), _ptr(W), _ptr(u), _ptr(out))
+    return out.reshape(np.shape(u))
+
+
+def gershgorin_dt(g: Grid, S, W):
+    """(dt_Euler, |lambda|max bound) from App. B's row-sum Gershgorin bound."""
+    S, W = _f64(S), _f64(W)
+    lam = ctypes.c_double(0.0)
+    dt = _load().or_gershgorin_dt(*g._dims(), _ptr(S), _ptr(W), ctypes.byref(lam))
+    return dt, lam.value
+
+
+def rkl2_stages(ratio: float, force_odd: bool = False) -> int:
+    return _load().or_rkl2_stages(float(ratio), 1 if force_odd else 0)
+
+
+def rkl2_coeffs(s: int):
+    """(mu, nu, mu~, gamma~) arrays indexed by stage j = 0..s."""
+    arrs = [np.zeros(s + 1) for _ in range(4)]
+    _load().or_rkl2_coeffs(int(s), *[_ptr(a) for a in arrs])
+    return tuple(arrs)
+
+
+def rkl2_superstep(g: Grid, S, W, u, dt: float, s: int) -> np.ndarray:
+    S, W = _f64(S), _f64(W)
+    out = _f64(u).copy()
+    rc = _load().or_rkl2_superstep(*g._dims(), _ptr(S), _ptr(W), _ptr(out), float(dt), int(s))
+    if rc != 0:
+        raise ValueError("s must be >= 2")
+    return out
+
+
+def build_A(S, W, dt: float) -> np.ndarray:
+    A = np.asarray(S, dtype=np.float64) * dt
+    A[:, 0] += W
+    return A
+
+
+def bilu0_factor(g: Grid, A, block) -> np.ndarray:
+    A = _f64(A)
+    blk = np.asarray(block, dtype=np.int32)
+    LU = np.empty_like(A)
+    rc = _load().or_bilu0_factor(*g._dims(), _ptr(blk), _ptr(A), _ptr(LU))
+    if rc != 0:
+        raise ValueError("grid not divisible by block")
+    return LU
+
+
+def bilu0_apply(g: Grid, LU, block, r) -> np.ndarray:
+    LU, r = _f64(LU), _f64(r)
+    blk = np.asarray(block, dtype=np.int32)
+    z = np.empty(g.N)
+    _load().or_bilu0_apply(*g._dims(), _ptr(blk), _ptr(LU), _ptr(r), _ptr(z))
+    return z.reshape(np.shape(r))
+
+
+def be_pcg(g: Grid, S, W, u, dt: float, pc: int = PC_JACOBI, block=(8, 8, 8), rtol: float = 1e-10,
+           maxit: int = 10000, x0=None, fixed_iters: int = 0):
+    """BE step by PCG; returns (x, iters, relres, status)."""
+    S, W = _f64(S), _f64(W)
+    x = _f64(u).copy()
+    blk = np.asarray(block, dtype=np.int32)
+    x0a = _f64(x0) if x0 is not None else None
+    x0p = _ptr(x0a) if x0a is not None else None
+    it = ctypes.c_int(0)
+    rel = ctypes.c_double(0.0)
+    st = _load().or_be_pcg(*g._dims(), _ptr(S), _ptr(W), _ptr(x), float(dt), int(pc), _ptr(blk),
+                           float(rtol), int(maxit), x0p, int(fixed_iters), ctypes.byref(it),
+                           ctypes.byref(rel))
+    if st < 0:
+        raise ValueError("bad PCG arguments")
+    return x, it.value, rel.value, st
+
+
+def dense(g: Grid, S19) -> np.ndarray:
+    """Dense N x N matrix of a 19-slot operator (tiny grids only)."""
+    off = offsets()
+    N = g.N
+    Dm = np.zeros((N, N))
+    nr, nth, nph = g.nr, g.nth, g.nph
+    for k in range(nph):
+        for j in range(nth):
+            for i in range(nr):
+                c = (k * nth + j) * nr + i
+                for s in range(NSLOT):
+                    ii, jj, kk = i + off[s, 0], j + off[s, 1], (k + off[s, 2]) % nph
+                    if 0 <= ii < nr and 0 <= jj < nth:
+                        Dm[c, (kk * nth + jj) * nr + ii] += S19[c, s]
+    return Dm
