@@ -1,0 +1,132 @@
+/*
+ * rklpcg.h -- C ABI of the GB300 (sm_103a) library that advances frozen-coefficient
+ * parabolic operators u_t = F(u) on a logically rectangular spherical (r, theta, phi)
+ * grid by RKL2 super-time-stepping or by backward Euler + preconditioned CG, after
+ * Caplan, Mikic, Linker & Lionello, arXiv:1610.01265.
+ *
+ * Operators (Sec. 4.1, boxed blue terms):
+ *   conduction  F(T) = (1/(3 k n)) div(kappa0 T^{5/2} bhat bhat . grad T)
+ *   viscosity   F(v) = (1/rho) div(nu rho grad v), per Cartesian component of v
+ * discretised with coefficients frozen at the start of a large step (lagged
+ * diffusivity, Sec. 1) so that F(u) = M u, M = -W^{-1} S, with S symmetric positive
+ * semi-definite (19-point anisotropic stencil for conduction, App. B p = 19;
+ * 7-point for viscosity) and W the cell heat capacity (3 k n V) or mass (rho V).
+ *
+ * Grid and layout.  nr x nth x nph cells; radial faces given by the caller (any
+ * strictly increasing positive radii, in units of R_sun = 6.96e10 cm); theta faces
+ * j pi / nth (cell-centred, zero-area pole faces); phi faces k 2 pi / nph, periodic.
+ * Zero-flux boundaries at the first and last radial face.  Every field is a
+ * contiguous float64 array indexed ((k * nth) + j) * nr + i, r fastest; a field of
+ * ncomp components is ncomp such arrays back to back.
+ *
+ * Memory.  Array arguments may be CUDA device pointers (the fast path) or host
+ * pointers (pageable or pinned); host arrays are copied through device buffers owned
+ * by the context on the context's stream inside the call, which then returns only
+ * after the result is back in host memory.  The library never frees, and never
+ * keeps after the call returns, any caller pointer.  With device pointers every
+ * call is asynchronous on the context's stream except for the scalar outputs
+ * (*_out), which are valid when the call returns.
+ *
+ * Errors.  Every entry point returns RKL_OK (0) or a negative RKL_E* code; nothing
+ * aborts or throws across the ABI.  rkl_strerror() names a code and
+ * rkl_last_error() gives the context's last detailed message.  Device-side failures
+ * (non-finite inputs, CG breakdown, non-convergence) are reported through a status
+ * word written by the kernels, never by trapping the GPU.  A context is not
+ * thread-safe: one host thread at a time.
+ */
+#ifndef RKLPCG_H
+#define RKLPCG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rkl_ctx rkl_ctx;
+
+typedef struct {
+  int nr, nth, nph;       /* cells along r, theta, phi: nr >= 1, nth >= 1, nph >= 3 */
+  const double *r_faces;  /* HOST array of nr+1 radial faces (R_sun), copied at create */
+} rkl_grid;
+
+enum {
+  RKL_OK = 0,
+  RKL_EINVAL = -1,     /* bad argument (null pointer, size, dt, s, block ...) */
+  RKL_ENOMEM = -2,     /* device allocation failed */
+  RKL_ECUDA = -3,      /* a CUDA runtime call failed (see rkl_last_error) */
+  RKL_ENONFINITE = -4, /* NaN/Inf or non-positive T, n, rho, nu found in the inputs */
+  RKL_ENOTCONV = -5,   /* PCG reached maxit without meeting rtol (u holds x_maxit) */
+  RKL_EBREAKDOWN = -6, /* PCG breakdown: p.Ap <= 0 or not finite (u holds the last x) */
+  RKL_ESTATE = -7      /* call out of order (e.g. a solver before set_coeffs) */
+};
+
+enum { RKL_OP_CONDUCTION = 0, RKL_OP_VISCOSITY = 1 };
+enum { RKL_PC_JACOBI = 1, RKL_PC_BILU0 = 2 };
+enum { RKL_F64 = 0 };
+
+#define RKL_BETA_TCUT 1 /* set_coeffs: evaluate kappa at max(T, 5e5 K) (Sec. 4.1 beta_Tcut) */
+#define RKL_FORCE_ODD 1 /* rkl2_superstep: round s up to an odd number (Sec. 3) */
+
+/* Create a context for one grid on the current CUDA device.  prec must be RKL_F64.
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream) on which all work of
+ * this context is queued.  Allocates the geometry tables; coefficient, stage and
+ * Krylov buffers are allocated on first use and kept until rkl_destroy. */
+int rkl_create(rkl_ctx **ctx, const rkl_grid *g, int prec, void *cuda_stream);
+
+/* Synchronise the context's stream and free everything it owns. NULL is a no-op. */
+int rkl_destroy(rkl_ctx *ctx);
+
+/* Re-bind the context to another stream (subsequent calls only). */
+int rkl_set_stream(rkl_ctx *ctx, void *cuda_stream);
+
+const char *rkl_strerror(int code);
+const char *rkl_last_error(const rkl_ctx *ctx);
+
+/* Eq. 5 (Sec. 3): number of RKL2 stages for dt/dt_exp, read as
+ * s = ceil((sqrt(9 + 16 dt/dt_exp) - 1) / 2), at least 2, odd with RKL_FORCE_ODD.
+ * Returns s, or RKL_EINVAL for a non-positive or non-finite ratio. */
+int rkl2_stage_count(double dt_over_dt_exp, int flags);
+
+/* Freeze the operator's coefficients for one large step (lagged diffusivity, Sec. 1;
+ * Sec. 4.1 for the coefficients) and compute the explicit Euler limit
+ * dt_exp = 2 / max_i sum_j |M_ij| (App. B, Eqs. 6-7, Gershgorin row sums).
+ *   op = RKL_OP_CONDUCTION: a = T [N] (K), b = bhat [3N] (r, theta, phi unit-vector
+ *        components), c = n [N] (cm^-3), kappa0 (cgs, 9e-7 in the paper);
+ *        flags may hold RKL_BETA_TCUT.
+ *   op = RKL_OP_VISCOSITY:  a = rho [N] (g cm^-3), b = NULL, c = nu [N] (cm^2/s);
+ *        kappa0 and flags are ignored.
+ * dt_exp_out (host, may be NULL) receives dt_exp in seconds.  Invalidates any
+ * cached preconditioner.  RKL_ENONFINITE if an input is NaN/Inf or T, n, rho, nu <= 0. */
+int set_coeffs(rkl_ctx *ctx, int op, const double *a, const double *b, const double *c,
+               double kappa0, int flags, double *dt_exp_out);
+
+/* Fu = F(u) = -W^{-1} S u for each of ncomp components (Eq. 1).  u and Fu must not
+ * overlap.  One stencil pass per component. */
+int apply_F(rkl_ctx *ctx, const double *u, double *Fu, int ncomp);
+
+/* In place u <- Y_s, one RKL2 super-step of size dt (Fig. 2, coefficients of Sec. 3,
+ * with the M0 weight gamma~_j = -(1 - b_{j-1}) mu~_j).  s > 0 uses exactly s stages
+ * (s >= 2); s == 0 takes s from Eq. 5 with dt/dt_exp (and RKL_FORCE_ODD in flags).
+ * s_used (host, may be NULL) receives the number of stages run.  Stability needs
+ * dt <= dt_exp (s^2 + s - 2)/4, which Eq. 5 guarantees when dt_exp is set_coeffs'. */
+int rkl2_superstep(rkl_ctx *ctx, double *u, int ncomp, double dt, double dt_exp, int s,
+                   int flags, int *s_used);
+
+/* In place backward-Euler step (Eqs. 2-4): solve (W + dt S) x = W u for each
+ * component by PCG (Fig. 1), from x0 (or from u when x0 is NULL), stopping when
+ * ||r||_2 <= rtol ||W u||_2 (tested after r.z as in Fig. 1) or after maxit
+ * products A p.  pc = RKL_PC_JACOBI (PC1) or RKL_PC_BILU0 (PC2: zero-fill ILU of
+ * every block[0] x block[1] x block[2] sub-domain, couplings between blocks and
+ * across the phi seam dropped, App. A); block is ignored for PC1 and the grid must
+ * be divisible by it for PC2.  rtol <= 0 runs exactly maxit iterations.
+ * iters_out / relres_out (host, may be NULL) receive ncomp values each: the number
+ * of A p products and the final ||r||/||W u||.  Returns RKL_ENOTCONV if some
+ * component did not converge, RKL_EBREAKDOWN on p.Ap <= 0. */
+int be_pcg_solve(rkl_ctx *ctx, double *u, int ncomp, double dt, int pc, const int block[3],
+                 double rtol, int maxit, const double *x0, int *iters_out,
+                 double *relres_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RKLPCG_H */

@@ -64,9 +64,9 @@ def _load():
             lib.or_rkl2_stages.argtypes = [D, I]
             lib.or_rkl2_coeffs.argtypes = [I, P, P, P, P]
             lib.or_rkl2_superstep.argtypes = [I, I, I, P, P, P, P, D, I]
-            lib.or_bilu0_factor.argtypes = [I, I, I, P, P, P, P]
-            lib.or_bilu0_apply.argtypes = [I, I, I, P, P, P, P, P]
-            lib.or_be_pcg.argtypes = [I, I, I, P, P, P, P, D, I, P, D, I, P, I, P, P]
+            lib.or_bilu0_factor.argtypes = [I, I, I, P, P, I, P, P]
+            lib.or_bilu0_apply.argtypes = [I, I, I, P, P, I, P, P, P]
+            lib.or_be_pcg.argtypes = [I, I, I, P, P, P, P, D, I, P, I, D, I, P, I, P, P]
             lib.or_offsets.argtypes = [P]
             lib.or_num_threads.restype = I
             _lib = lib
@@ -185,27 +185,29 @@ def build_A(S, W, dt: float) -> np.ndarray:
     return A
 
 
-def bilu0_factor(g: Grid, A, block) -> np.ndarray:
+def bilu0_factor(g: Grid, A, block, pattern: int = 19) -> np.ndarray:
+    """Zero-fill ILU of every block; pattern = 19 (conduction) or 7 (viscosity)."""
     A = _f64(A)
     blk = np.asarray(block, dtype=np.int32)
     LU = np.empty_like(A)
-    rc = _load().or_bilu0_factor(*g._dims(), _ptr(blk), _ptr(A), _ptr(LU))
+    rc = _load().or_bilu0_factor(*g._dims(), _ptr(blk), int(pattern), _ptr(A), _ptr(LU))
     if rc != 0:
         raise ValueError("grid not divisible by block")
     return LU
 
 
-def bilu0_apply(g: Grid, LU, block, r) -> np.ndarray:
+def bilu0_apply(g: Grid, LU, block, r, pattern: int = 19) -> np.ndarray:
     LU, r = _f64(LU), _f64(r)
     blk = np.asarray(block, dtype=np.int32)
     z = np.empty(g.N)
-    _load().or_bilu0_apply(*g._dims(), _ptr(blk), _ptr(LU), _ptr(r), _ptr(z))
+    _load().or_bilu0_apply(*g._dims(), _ptr(blk), int(pattern), _ptr(LU), _ptr(r), _ptr(z))
     return z.reshape(np.shape(r))
 
 
 def be_pcg(g: Grid, S, W, u, dt: float, pc: int = PC_JACOBI, block=(8, 8, 8), rtol: float = 1e-10,
-           maxit: int = 10000, x0=None, fixed_iters: int = 0):
-    """BE step by PCG; returns (x, iters, relres, status)."""
+           maxit: int = 10000, x0=None, fixed_iters: int = 0, pattern: int = 19):
+    """BE step by PCG; returns (x, iters, relres, status).  pattern: 19 (conduction) or 7
+    (viscosity), the structural pattern kept by the PC2 zero-fill ILU."""
     S, W = _f64(S), _f64(W)
     x = _f64(u).copy()
     blk = np.asarray(block, dtype=np.int32)
@@ -214,7 +216,7 @@ def be_pcg(g: Grid, S, W, u, dt: float, pc: int = PC_JACOBI, block=(8, 8, 8), rt
     it = ctypes.c_int(0)
     rel = ctypes.c_double(0.0)
     st = _load().or_be_pcg(*g._dims(), _ptr(S), _ptr(W), _ptr(x), float(dt), int(pc), _ptr(blk),
-                           float(rtol), int(maxit), x0p, int(fixed_iters), ctypes.byref(it),
+                           int(pattern), float(rtol), int(maxit), x0p, int(fixed_iters), ctypes.byref(it),
                            ctypes.byref(rel))
     if st < 0:
         raise ValueError("bad PCG arguments")

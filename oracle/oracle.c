@@ -441,10 +441,16 @@ static void build_A(const grid *g, const double *S, const double *W, double dt, 
   }
 }
 
-/* is the slot-s neighbour of (i,j,k) inside the same block (no phi wrap)? */
+/* Structural pattern of the operator: 19 points (conduction) or the 7 points of the
+   centre and face neighbours (viscosity); App. A's "LU_ij != 0" means this pattern. */
+static int g_npat = 19;
+
+/* is the slot-s neighbour of (i,j,k) inside the same block (no phi wrap) and in the
+   operator's pattern? */
 static int in_block(const grid *g, const int *blk, int i, int j, int k, int s) {
   int ii = i + OFF[s][0], jj = j + OFF[s][1], kk = k + OFF[s][2];
   (void)g;
+  if (g_npat == 7 && s >= 7) return 0;
   if (ii < 0 || jj < 0 || kk < 0) return 0;
   if (ii / blk[0] != i / blk[0] || jj / blk[1] != j / blk[1] || kk / blk[2] != k / blk[2])
     return 0;
@@ -477,9 +483,11 @@ static int slot_by_offset(int di, int dj, int dk) {
 
 /* zero-fill IKJ ILU of every block of A (App. A, PC2); LU uses the 19-slot layout and
    only slots inside the block are meaningful (others are set to zero). */
-int or_bilu0_factor(int nr, int nth, int nph, const double *rf, const int *blk,
+int or_bilu0_factor(int nr, int nth, int nph, const double *rf, const int *blk, int npat,
                     const double *A, double *LU) {
   grid g = {nr, nth, nph, rf};
+  if (npat != 19 && npat != 7) return -1;
+  g_npat = npat;
   long N = ncell(&g);
   if (nr % blk[0] || nth % blk[1] || nph % blk[2]) return -1;
   for (long c = 0; c < N * NS; c++) LU[c] = 0.0;
@@ -521,9 +529,11 @@ int or_bilu0_factor(int nr, int nth, int nph, const double *rf, const int *blk,
   return 0;
 }
 
-int or_bilu0_apply(int nr, int nth, int nph, const double *rf, const int *blk,
+int or_bilu0_apply(int nr, int nth, int nph, const double *rf, const int *blk, int npat,
                    const double *LU, const double *r, double *z) {
   grid g = {nr, nth, nph, rf};
+  if (npat != 19 && npat != 7) return -1;
+  g_npat = npat;
   int nbk = nph / blk[2], nbj = nth / blk[1], nbi = nr / blk[0];
 #pragma omp parallel for schedule(dynamic) collapse(3)
   for (int bk = 0; bk < nbk; bk++)
@@ -572,14 +582,16 @@ static double dot(long N, const double *a, const double *b) {
  * ILU0 with block dims blk).  Stops when ||r||_2 <= rtol ||b||_2 (checked after r.z, the
  * order of Fig. 1) or after maxit products A p.  fixed_iters > 0 runs exactly that many
  * iterations with no convergence test.  Returns 0 converged, 1 maxit reached,
- * 2 breakdown (p.Ap <= 0 or not finite), -1 bad arguments.
+ * 2 breakdown (p.Ap <= 0 or not finite), -1 bad arguments.  npat = 19 (conduction) or
+ * 7 (viscosity) is the operator's structural pattern used by PC2.
  */
 int or_be_pcg(int nr, int nth, int nph, const double *rf, const double *S, const double *W,
-              double *u, double dt, int pc, const int *blk, double rtol, int maxit,
+              double *u, double dt, int pc, const int *blk, int npat, double rtol, int maxit,
               const double *x0, int fixed_iters, int *iters_out, double *relres_out) {
   grid g = {nr, nth, nph, rf};
   long N = ncell(&g);
   if (pc != 1 && pc != 2) return -1;
+  if (npat != 19 && npat != 7) return -1;
   if (pc == 2 && (nr % blk[0] || nth % blk[1] || nph % blk[2])) return -1;
   double *A = malloc(sizeof(double) * N * NS), *LU = NULL;
   double *b = malloc(sizeof(double) * N), *x = malloc(sizeof(double) * N);
@@ -588,7 +600,7 @@ int or_be_pcg(int nr, int nth, int nph, const double *rf, const double *S, const
   build_A(&g, S, W, dt, A);
   if (pc == 2) {
     LU = malloc(sizeof(double) * N * NS);
-    or_bilu0_factor(nr, nth, nph, rf, blk, A, LU);
+    or_bilu0_factor(nr, nth, nph, rf, blk, npat, A, LU);
   }
   for (long c = 0; c < N; c++) {
     b[c] = W[c] * u[c];
@@ -601,7 +613,7 @@ int or_be_pcg(int nr, int nth, int nph, const double *rf, const double *S, const
     if (pc == 1)                                                     \
       for (long c = 0; c < N; c++) z[c] = r[c] / A[c * NS];          \
     else                                                             \
-      or_bilu0_apply(nr, nth, nph, rf, blk, LU, r, z);               \
+      or_bilu0_apply(nr, nth, nph, rf, blk, npat, LU, r, z);         \
   } while (0)
   PRECOND();
   for (long c = 0; c < N; c++) p[c] = z[c];

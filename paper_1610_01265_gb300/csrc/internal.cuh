@@ -1,0 +1,165 @@
+// internal.cuh -- shared definitions of the rklpcg CUDA library (not part of the ABI).
+//
+// Operator storage.  The frozen operator is M = -W^{-1} S with S symmetric positive
+// semi-definite.  S is kept once per cell as its "forward" off-diagonal entries (to
+// the neighbours at lexicographically positive offsets) plus its diagonal, in
+// structure-of-arrays form coef[slot * N + cell]:
+//   conduction (19-point): 9 forward slots FWD[0..8] + diagonal in slot 9
+//   viscosity  (7-point):  3 forward slots FWD[0..2] + diagonal in slot 3
+// The entry of row c towards c - FWD[m] is the forward entry FWD[m] stored at the
+// neighbour c - FWD[m], so S is exactly symmetric by construction.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/rklpcg.h"
+
+#define RKL_RSUN_CM 6.96e10
+#define RKL_KBOLTZ 1.380649e-16
+#define RKL_TCUT 5.0e5
+#define RKL_PI 3.14159265358979323846
+
+namespace rkl {
+
+// lexicographically positive neighbour offsets FWD[m] = (di, dj, dk) along (r, theta, phi):
+//   m: 0 (1,0,0)  1 (0,1,0)  2 (0,0,1)  3 (-1,1,0)  4 (1,1,0)
+//      5 (-1,0,1) 6 (1,0,1)  7 (0,-1,1) 8 (0,1,1)
+__host__ __device__ constexpr int fwd_di(int m) {
+  return (m == 0 || m == 4 || m == 6) ? 1 : ((m == 3 || m == 5) ? -1 : 0);
+}
+__host__ __device__ constexpr int fwd_dj(int m) {
+  return (m == 1 || m == 3 || m == 4 || m == 8) ? 1 : (m == 7 ? -1 : 0);
+}
+__host__ __device__ constexpr int fwd_dk(int m) { return (m == 2 || m >= 5) ? 1 : 0; }
+
+enum { NCOEF_COND = 10, NCOEF_VISC = 4 };
+
+struct Dims {
+  int nr, nth, nph;
+  long long N;
+  long long nrt;  // nr * nth (one phi layer)
+};
+
+// Geometry tables in cm (device pointers); built on the host at rkl_create.
+struct Geo {
+  const double *rc;    // [nr]   cell-centre radius
+  const double *hr;    // [nr]   rc[i+1] - rc[i] (last entry unused)
+  const double *dr;    // [nr]   span of the centred r-difference (mirror ghosts at ends)
+  const double *ar;    // [nr]   rf[i+1]^2 (r-face area over the solid angle)
+  const double *a2;    // [nr]   (rf[i+1]^2 - rf[i]^2)/2
+  const double *v3;    // [nr]   (rf[i+1]^3 - rf[i]^3)/3
+  const double *dcos;  // [nth]  cos(theta_j) - cos(theta_{j+1}) (faces)
+  const double *stf;   // [nth]  sin of the upper theta face
+  const double *stc;   // [nth]  sin of the cell-centre theta
+  double dth, dph;
+};
+
+// Scalars of one PCG solve, resident on the device.
+struct PcgState {
+  double rr;       // r.z
+  double rnorm2;   // r.r
+  double bnorm2;   // (W u).(W u)
+  double pAp;
+  double alpha, beta;
+  double rtol2;    // rtol^2 (<= 0: never converge)
+  int iters;
+  int maxit;
+  int status;      // 0 running, 1 converged, 2 breakdown, 3 maxit reached
+  int pad;
+};
+
+enum { PCG_RUNNING = 0, PCG_CONVERGED = 1, PCG_BREAKDOWN = 2, PCG_MAXIT = 3 };
+
+// block-ILU0 level schedule of one block shape (device pointers)
+struct IluPlan {
+  int bi, bj, bk, bs;     // block dims and cells per block
+  int nlev;               // number of wavefront levels
+  int nbi, nbj, nbk;      // blocks along r, theta, phi
+  const int *lev_start;   // [nlev+1] offsets into lev_cell
+  const int *lev_cell;    // [bs] block-local index (li + bi*(lj + bj*lk)) in level order
+  const int *pos_of;      // [bs] level-order position of a block-local index
+};
+
+}  // namespace rkl
+
+struct rkl_ctx {
+  rkl::Dims d;
+  int device;
+  cudaStream_t stream;
+  std::string err;
+  std::vector<double> rf;
+  int nsm;
+
+  // geometry
+  double *geo_buf = nullptr;
+  rkl::Geo geo;
+
+  // frozen operator
+  int op = -1;  // RKL_OP_* once set_coeffs succeeded
+  double dt_exp = 0.0;
+  double *coef = nullptr;   // NCOEF_COND * N (also used for viscosity)
+  double *W = nullptr;      // N
+  double *invW = nullptr;   // N
+  double *scratch = nullptr;  // 10 * N: kappa/mu + face scalars during set_coeffs
+  unsigned long long *d_lammax = nullptr;
+  int *d_flag = nullptr;
+
+  // RKL2
+  double *M0 = nullptr, *Ya = nullptr, *Yb = nullptr;
+
+  // PCG
+  double *r = nullptr, *p = nullptr, *y = nullptr, *zbuf = nullptr, *dinv = nullptr;
+  double *partials = nullptr;
+  int npart = 0;
+  unsigned int *counter = nullptr;
+  rkl::PcgState *d_state = nullptr;
+  rkl::PcgState *h_state = nullptr;  // pinned
+
+  // block ILU0
+  double *LU = nullptr;
+  int *plan_buf = nullptr;
+  rkl::IluPlan plan{};
+  int lu_blk[3] = {0, 0, 0};
+  double lu_dt = 0.0;
+  int lu_valid = 0;
+
+  // host-pointer staging
+  double *stage = nullptr;
+  size_t stage_cap = 0;  // doubles
+  double *stage2 = nullptr;
+  size_t stage2_cap = 0;
+};
+
+namespace rkl {
+
+int set_error(rkl_ctx *ctx, int code, const std::string &msg);
+int cuda_check(rkl_ctx *ctx, cudaError_t e, const char *what);
+int ensure_buffer(rkl_ctx *ctx, double **buf, size_t count, const char *what);
+
+inline unsigned int grid_for(long long n, int block) {
+  return (unsigned int)((n + block - 1) / block);
+}
+
+// ---- launch wrappers (defined in the .cu files) ----
+// coeffs.cu
+int launch_setup_conduction(rkl_ctx *ctx, const double *T, const double *bhat, const double *n,
+                            double kappa0, int flags);
+int launch_setup_viscosity(rkl_ctx *ctx, const double *rho, const double *nu);
+
+// rkl2.cu
+int launch_apply_F(rkl_ctx *ctx, const double *u, double *Fu);
+int launch_rkl2_stage1(rkl_ctx *ctx, const double *Y0, double *M0, double *Y1, double mut1dt);
+int launch_rkl2_stage(rkl_ctx *ctx, const double *Ym1, const double *Ym2, const double *Y0,
+                      const double *M0, double *Yout, double mu, double nu, double mutdt,
+                      double gtdt);
+
+// pcg.cu
+int pcg_solve_component(rkl_ctx *ctx, double *x, const double *u, const double *x0, double dt,
+                        int pc, double rtol, int maxit, int *iters, double *relres,
+                        int *status);
+int bilu0_prepare(rkl_ctx *ctx, const int *block, double dt);
+
+}  // namespace rkl

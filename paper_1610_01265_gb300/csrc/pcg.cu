@@ -1,0 +1,512 @@
+// pcg.cu -- backward Euler by preconditioned CG (Sec. 2, Eqs. 2-4, Fig. 1) with point
+// Jacobi (PC1) or non-overlapping block ILU0 (PC2, App. A).
+//
+// System: (W + dt S) x = W u^n, the W-scaled symmetric form of Eq. 4.  Every scalar
+// of the iteration (alpha, beta, r.z, the residual norm, the status) stays on the
+// device: each dot product is a deterministic two-level reduction (fixed-order block
+// sums, then the last block to finish sums the block partials in a fixed order).
+// Kernels of an iteration read the status word first and return at once when the
+// solve has converged, broken down or hit maxit, so the host launches iterations in
+// chunks and reads the status back once per chunk.
+//
+// Block ILU0: one CTA per sub-domain block; rows are processed in wavefronts
+// l = li + 2 lj + 3 lk (every lower neighbour of the 19-point pattern has a smaller
+// l), the factors are stored per block in wavefront order so that a wavefront's rows
+// are contiguous, and the triangular solves run in shared memory.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "internal.cuh"
+#include "stencil.cuh"
+
+namespace rkl {
+
+namespace {
+
+constexpr int RB = 256;   // block size of grid-stride reduction kernels
+constexpr int IB = 64;    // block size of the block-ILU0 kernels
+constexpr int NSL = 19;   // slots of an ILU row: 0 diag, 1+m = -FWD[m], 10+m = +FWD[m]
+
+__device__ __forceinline__ int slot_di(int s) { return s == 0 ? 0 : (s < 10 ? -fwd_di(s - 1) : fwd_di(s - 10)); }
+__device__ __forceinline__ int slot_dj(int s) { return s == 0 ? 0 : (s < 10 ? -fwd_dj(s - 1) : fwd_dj(s - 10)); }
+__device__ __forceinline__ int slot_dk(int s) { return s == 0 ? 0 : (s < 10 ? -fwd_dk(s - 1) : fwd_dk(s - 10)); }
+
+// Sum NV per-thread values over the whole grid.  Returns true (in every thread of the
+// last block to finish) with the totals in tot[] of thread 0.
+template <int NV, int BS>
+__device__ bool grid_sum(double (&v)[NV], double *partials, unsigned int *counter,
+                         double (&tot)[NV]) {
+  __shared__ double sh[NV][BS / 32];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NV; q++) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_down_sync(0xffffffffu, v[q], o);
+    if (lane == 0) sh[q][warp] = v[q];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; q++) {
+      double s = 0.0;
+      for (int w = 0; w < BS / 32; w++) s += sh[q][w];
+      partials[(size_t)blockIdx.x * NV + q] = s;
+    }
+    __threadfence();
+    unsigned int t = atomicAdd(counter, 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+#pragma unroll
+  for (int q = 0; q < NV; q++) {
+    double s = 0.0;
+    for (unsigned int b = threadIdx.x; b < gridDim.x; b += BS) s += __ldcg(&partials[(size_t)b * NV + q]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) sh[q][warp] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; q++) {
+      double s = 0.0;
+      for (int w = 0; w < BS / 32; w++) s += sh[q][w];
+      tot[q] = s;
+    }
+    *counter = 0u;
+  }
+  return true;
+}
+
+// r.z and r.r after a preconditioner application: the convergence test of Fig. 1
+__device__ void finalize_dots(PcgState *st, double rz, double rn, bool init) {
+  if (init) {
+    st->rr = rz;
+    st->rnorm2 = rn;
+    st->iters = 0;
+    if (!isfinite(rz) || !isfinite(rn)) st->status = PCG_BREAKDOWN;
+    else st->status = (rn <= st->rtol2 * st->bnorm2) ? PCG_CONVERGED : PCG_RUNNING;
+    return;
+  }
+  double rold = st->rr;
+  st->rr = rz;
+  st->rnorm2 = rn;
+  st->iters += 1;
+  if (!isfinite(rz) || !isfinite(rn)) st->status = PCG_BREAKDOWN;
+  else if (rn <= st->rtol2 * st->bnorm2) st->status = PCG_CONVERGED;
+  else if (st->iters >= st->maxit) st->status = PCG_MAXIT;
+  else st->beta = rz / rold;
+}
+
+// r0 = W u - (W x0 + dt S x0); ||W u||^2; Jacobi diagonal 1/(W + dt S_cc)
+template <int OP>
+__global__ void __launch_bounds__(RB) k_r0(Dims d, const double *__restrict__ coef,
+                                           const double *__restrict__ W, double dt,
+                                           const double *u, const double *x0,
+                                           double *__restrict__ r, double *__restrict__ dinv,
+                                           double *partials, unsigned int *counter,
+                                           PcgState *st) {
+  double v[1] = {0.0};
+  for (long long c = (long long)blockIdx.x * RB + threadIdx.x; c < d.N; c += (long long)gridDim.x * RB) {
+    int i, j, k;
+    cell_coords(d, c, i, j, k);
+    Nbr n = neighbours(d, i, j, k);
+    double w = W[c];
+    double ax = fma(w, x0[c], dt * S_apply<OP>(d, coef, x0, c, n));
+    double b = w * u[c];
+    r[c] = b - ax;
+    if (dinv) dinv[c] = 1.0 / fma(dt, S_diag<OP>(d, coef, c), w);
+    v[0] = fma(b, b, v[0]);
+  }
+  double tot[1];
+  if (grid_sum<1, RB>(v, partials, counter, tot) && threadIdx.x == 0) st->bnorm2 = tot[0];
+}
+
+__global__ void __launch_bounds__(RB) k_jacobi_init(long long N, const double *__restrict__ r,
+                                                    const double *__restrict__ dinv,
+                                                    double *__restrict__ p, double *partials,
+                                                    unsigned int *counter, PcgState *st) {
+  double v[2] = {0.0, 0.0};
+  for (long long c = (long long)blockIdx.x * RB + threadIdx.x; c < N; c += (long long)gridDim.x * RB) {
+    double rv = r[c], z = rv * dinv[c];
+    p[c] = z;
+    v[0] = fma(rv, z, v[0]);
+    v[1] = fma(rv, rv, v[1]);
+  }
+  double tot[2];
+  if (grid_sum<2, RB>(v, partials, counter, tot) && threadIdx.x == 0) finalize_dots(st, tot[0], tot[1], true);
+}
+
+// y = A p = W p + dt S p ; alpha = r.z / p.y
+template <int OP>
+__global__ void __launch_bounds__(RB) k_spmv(Dims d, const double *__restrict__ coef,
+                                             const double *__restrict__ W, double dt,
+                                             const double *__restrict__ p,
+                                             double *__restrict__ y, double *partials,
+                                             unsigned int *counter, PcgState *st) {
+  if (st->status != PCG_RUNNING) return;
+  double v[1] = {0.0};
+  for (long long c = (long long)blockIdx.x * RB + threadIdx.x; c < d.N; c += (long long)gridDim.x * RB) {
+    int i, j, k;
+    cell_coords(d, c, i, j, k);
+    Nbr n = neighbours(d, i, j, k);
+    double pc = p[c];
+    double yv = fma(W[c], pc, dt * S_apply<OP>(d, coef, p, c, n));
+    y[c] = yv;
+    v[0] = fma(pc, yv, v[0]);
+  }
+  double tot[1];
+  if (grid_sum<1, RB>(v, partials, counter, tot) && threadIdx.x == 0) {
+    double pAp = tot[0];
+    st->pAp = pAp;
+    if (!(pAp > 0.0) || !isfinite(pAp)) st->status = PCG_BREAKDOWN;
+    else st->alpha = st->rr / pAp;
+  }
+}
+
+// x += alpha p ; r -= alpha y ; z = r / diag(A) ; r.z, r.r
+__global__ void __launch_bounds__(RB) k_update_jacobi(long long N, double *__restrict__ x,
+                                                      const double *__restrict__ p,
+                                                      double *__restrict__ r,
+                                                      const double *__restrict__ y,
+                                                      const double *__restrict__ dinv,
+                                                      double *partials, unsigned int *counter,
+                                                      PcgState *st) {
+  if (st->status != PCG_RUNNING) return;
+  const double a = st->alpha;
+  double v[2] = {0.0, 0.0};
+  for (long long c = (long long)blockIdx.x * RB + threadIdx.x; c < N; c += (long long)gridDim.x * RB) {
+    x[c] = fma(a, p[c], x[c]);
+    double rv = fma(-a, y[c], r[c]);
+    r[c] = rv;
+    double z = rv * dinv[c];
+    v[0] = fma(rv, z, v[0]);
+    v[1] = fma(rv, rv, v[1]);
+  }
+  double tot[2];
+  if (grid_sum<2, RB>(v, partials, counter, tot) && threadIdx.x == 0) finalize_dots(st, tot[0], tot[1], false);
+}
+
+__global__ void __launch_bounds__(RB) k_pupdate_jacobi(long long N, const double *__restrict__ r,
+                                                       const double *__restrict__ dinv,
+                                                       double *__restrict__ p,
+                                                       const PcgState *st) {
+  if (st->status != PCG_RUNNING) return;
+  const double b = st->beta;
+  for (long long c = (long long)blockIdx.x * RB + threadIdx.x; c < N; c += (long long)gridDim.x * RB)
+    p[c] = fma(b, p[c], r[c] * dinv[c]);
+}
+
+__global__ void __launch_bounds__(RB) k_xr_update(long long N, double *__restrict__ x,
+                                                  const double *__restrict__ p,
+                                                  double *__restrict__ r,
+                                                  const double *__restrict__ y,
+                                                  const PcgState *st) {
+  if (st->status != PCG_RUNNING) return;
+  const double a = st->alpha;
+  for (long long c = (long long)blockIdx.x * RB + threadIdx.x; c < N; c += (long long)gridDim.x * RB) {
+    x[c] = fma(a, p[c], x[c]);
+    r[c] = fma(-a, y[c], r[c]);
+  }
+}
+
+__global__ void __launch_bounds__(RB) k_pupdate_z(long long N, const double *__restrict__ z,
+                                                  double *__restrict__ p, const PcgState *st,
+                                                  int first) {
+  if (st->status != PCG_RUNNING) return;
+  const double b = first ? 0.0 : st->beta;
+  for (long long c = (long long)blockIdx.x * RB + threadIdx.x; c < N; c += (long long)gridDim.x * RB)
+    p[c] = first ? z[c] : fma(b, p[c], z[c]);
+}
+
+// ---------------- block ILU0 ----------------
+
+struct BlockCell {
+  int l, li, lj, lk;
+  long long c;
+};
+
+__device__ __forceinline__ BlockCell block_cell(const Dims &d, const IluPlan &pl, int blk, int p) {
+  BlockCell b;
+  int bI = blk % pl.nbi, bJ = (blk / pl.nbi) % pl.nbj, bK = blk / (pl.nbi * pl.nbj);
+  b.l = pl.lev_cell[p];
+  b.li = b.l % pl.bi;
+  b.lj = (b.l / pl.bi) % pl.bj;
+  b.lk = b.l / (pl.bi * pl.bj);
+  int i = bI * pl.bi + b.li, j = bJ * pl.bj + b.lj, k = bK * pl.bk + b.lk;
+  b.c = ((long long)k * d.nth + j) * d.nr + i;
+  return b;
+}
+
+// is the slot-s neighbour inside the block (no phi wrap), and part of the pattern
+template <int OP>
+__device__ __forceinline__ bool in_pattern(const IluPlan &pl, const BlockCell &b, int s) {
+  if (OP == RKL_OP_VISCOSITY && s != 0 && (((s - 1) % 9) >= 3)) return false;  // 7-point
+  int li = b.li + slot_di(s), lj = b.lj + slot_dj(s), lk = b.lk + slot_dk(s);
+  return li >= 0 && li < pl.bi && lj >= 0 && lj < pl.bj && lk >= 0 && lk < pl.bk;
+}
+
+__device__ __forceinline__ int slot_ldelta(const IluPlan &pl, int s) {
+  return slot_di(s) + pl.bi * (slot_dj(s) + pl.bj * slot_dk(s));
+}
+
+__device__ __forceinline__ int lex_rank(int s) {
+  return (slot_dk(s) + 1) * 9 + (slot_dj(s) + 1) * 3 + (slot_di(s) + 1);
+}
+
+__device__ __forceinline__ int slot_of_offset(int di, int dj, int dk) {
+  if (di == 0 && dj == 0 && dk == 0) return 0;
+  for (int m = 0; m < 9; m++) {
+    if (fwd_di(m) == di && fwd_dj(m) == dj && fwd_dk(m) == dk) return 10 + m;
+    if (fwd_di(m) == -di && fwd_dj(m) == -dj && fwd_dk(m) == -dk) return 1 + m;
+  }
+  return -1;
+}
+
+// zero-fill IKJ ILU of each block's rows of A = W + dt S (App. A)
+template <int OP>
+__global__ void __launch_bounds__(IB) k_bilu_factor(Dims d, IluPlan pl,
+                                                    const double *__restrict__ coef,
+                                                    const double *__restrict__ W, double dt,
+                                                    double *__restrict__ LU) {
+  const int blk = blockIdx.x;
+  const size_t base = (size_t)blk * NSL * pl.bs;
+  const int nf = OP == RKL_OP_CONDUCTION ? 9 : 3;
+  for (int lev = 0; lev < pl.nlev; lev++) {
+    for (int p = pl.lev_start[lev] + threadIdx.x; p < pl.lev_start[lev + 1]; p += IB) {
+      BlockCell b = block_cell(d, pl, blk, p);
+      double a[NSL];
+      a[0] = fma(dt, S_diag<OP>(d, coef, b.c), W[b.c]);
+      for (int m = 0; m < 9; m++) {
+        a[1 + m] = 0.0;
+        a[10 + m] = 0.0;
+        if (m >= nf) continue;
+        long long off = fwd_di(m) + (long long)fwd_dj(m) * d.nr + (long long)fwd_dk(m) * d.nrt;
+        if (in_pattern<OP>(pl, b, 10 + m)) a[10 + m] = dt * coef[m * d.N + b.c];
+        if (in_pattern<OP>(pl, b, 1 + m)) a[1 + m] = dt * coef[m * d.N + b.c - off];
+      }
+      // lower slots in increasing order of the neighbour's position (lexicographic)
+      for (int rk = 0; rk < 13; rk++) {
+        int s = -1;
+        for (int q = 1; q < 10; q++)
+          if (lex_rank(q) == rk) s = q;
+        if (s < 0 || !in_pattern<OP>(pl, b, s)) continue;
+        int kpos = pl.pos_of[b.l + slot_ldelta(pl, s)];
+        double L = a[s] / LU[base + kpos];
+        a[s] = L;
+        for (int q = 0; q < NSL; q++) {
+          if (lex_rank(q) <= rk || !in_pattern<OP>(pl, b, q)) continue;
+          int s3 = slot_of_offset(slot_di(q) - slot_di(s), slot_dj(q) - slot_dj(s),
+                                  slot_dk(q) - slot_dk(s));
+          if (s3 < 0) continue;
+          // (k, j) must be in row k's pattern; j = this row's neighbour q is in the block
+          if (OP == RKL_OP_VISCOSITY && s3 != 0 && (((s3 - 1) % 9) >= 3)) continue;
+          a[q] -= L * LU[base + (size_t)s3 * pl.bs + kpos];
+        }
+      }
+      for (int q = 0; q < NSL; q++)
+        LU[base + (size_t)q * pl.bs + p] = in_pattern<OP>(pl, b, q) ? a[q] : 0.0;
+    }
+    __syncthreads();
+  }
+}
+
+// z = (LU)^{-1} r on every block (forward unit-L, backward U), then r.z and r.r
+template <int OP>
+__global__ void __launch_bounds__(IB) k_bilu_apply(Dims d, IluPlan pl,
+                                                   const double *__restrict__ LU,
+                                                   const double *__restrict__ r,
+                                                   double *__restrict__ z, double *partials,
+                                                   unsigned int *counter, PcgState *st,
+                                                   int init) {
+  if (!init && st->status != PCG_RUNNING) return;
+  extern __shared__ double zs[];
+  const int blk = blockIdx.x;
+  const size_t base = (size_t)blk * NSL * pl.bs;
+  for (int lev = 0; lev < pl.nlev; lev++) {
+    for (int p = pl.lev_start[lev] + threadIdx.x; p < pl.lev_start[lev + 1]; p += IB) {
+      BlockCell b = block_cell(d, pl, blk, p);
+      double v = r[b.c];
+#pragma unroll
+      for (int s = 1; s < 10; s++)
+        if (in_pattern<OP>(pl, b, s)) v = fma(-LU[base + (size_t)s * pl.bs + p], zs[b.l + slot_ldelta(pl, s)], v);
+      zs[b.l] = v;
+    }
+    __syncthreads();
+  }
+  for (int lev = pl.nlev - 1; lev >= 0; lev--) {
+    for (int p = pl.lev_start[lev] + threadIdx.x; p < pl.lev_start[lev + 1]; p += IB) {
+      BlockCell b = block_cell(d, pl, blk, p);
+      double v = zs[b.l];
+#pragma unroll
+      for (int s = 10; s < NSL; s++)
+        if (in_pattern<OP>(pl, b, s)) v = fma(-LU[base + (size_t)s * pl.bs + p], zs[b.l + slot_ldelta(pl, s)], v);
+      zs[b.l] = v / LU[base + p];
+    }
+    __syncthreads();
+  }
+  double v2[2] = {0.0, 0.0};
+  for (int p = threadIdx.x; p < pl.bs; p += IB) {
+    BlockCell b = block_cell(d, pl, blk, p);
+    double zv = zs[b.l], rv = r[b.c];
+    z[b.c] = zv;
+    v2[0] = fma(rv, zv, v2[0]);
+    v2[1] = fma(rv, rv, v2[1]);
+  }
+  double tot[2];
+  if (grid_sum<2, IB>(v2, partials, counter, tot) && threadIdx.x == 0) finalize_dots(st, tot[0], tot[1], init != 0);
+}
+
+unsigned int stride_grid(const rkl_ctx *ctx) {
+  long long g = (ctx->d.N + RB - 1) / RB;
+  long long cap = (long long)ctx->nsm * 8;
+  return (unsigned int)std::max(1LL, std::min(g, cap));
+}
+
+}  // namespace
+
+// Build the wavefront plan of a block shape and (re)factor A = W + dt S when the block
+// shape, dt or the operator changed since the last factorisation.
+int bilu0_prepare(rkl_ctx *ctx, const int *block, double dt) {
+  const Dims &d = ctx->d;
+  if (ctx->lu_valid && ctx->lu_blk[0] == block[0] && ctx->lu_blk[1] == block[1] &&
+      ctx->lu_blk[2] == block[2] && ctx->lu_dt == dt)
+    return RKL_OK;
+  int bi = block[0], bj = block[1], bk = block[2], bs = bi * bj * bk;
+  if (ctx->plan.bs != bs || ctx->plan.bi != bi || ctx->plan.bj != bj || ctx->plan.bk != bk) {
+    int nlev = (bi - 1) + 2 * (bj - 1) + 3 * (bk - 1) + 1;
+    std::vector<int> start(nlev + 1, 0), cell(bs), pos(bs);
+    for (int lk = 0; lk < bk; lk++)
+      for (int lj = 0; lj < bj; lj++)
+        for (int li = 0; li < bi; li++) start[li + 2 * lj + 3 * lk + 1]++;
+    for (int l = 0; l < nlev; l++) start[l + 1] += start[l];
+    std::vector<int> fill(start.begin(), start.end() - 1);
+    for (int lk = 0; lk < bk; lk++)
+      for (int lj = 0; lj < bj; lj++)
+        for (int li = 0; li < bi; li++) {
+          int l = li + bi * (lj + bj * lk);
+          int p = fill[li + 2 * lj + 3 * lk]++;
+          cell[p] = l;
+          pos[l] = p;
+        }
+    if (ctx->plan_buf) cudaFree(ctx->plan_buf);
+    ctx->plan_buf = nullptr;
+    size_t nint = (size_t)(nlev + 1) + 2 * (size_t)bs;
+    if (cuda_check(ctx, cudaMalloc(&ctx->plan_buf, nint * sizeof(int)), "alloc ILU plan")) return RKL_ENOMEM;
+    std::vector<int> host(nint);
+    std::copy(start.begin(), start.end(), host.begin());
+    std::copy(cell.begin(), cell.end(), host.begin() + nlev + 1);
+    std::copy(pos.begin(), pos.end(), host.begin() + nlev + 1 + bs);
+    int rc = cuda_check(ctx, cudaMemcpyAsync(ctx->plan_buf, host.data(), nint * sizeof(int),
+                                             cudaMemcpyHostToDevice, ctx->stream),
+                        "upload ILU plan");
+    if (rc) return rc;
+    rc = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "upload ILU plan");
+    if (rc) return rc;
+    IluPlan &pl = ctx->plan;
+    pl.bi = bi; pl.bj = bj; pl.bk = bk; pl.bs = bs; pl.nlev = nlev;
+    pl.nbi = d.nr / bi; pl.nbj = d.nth / bj; pl.nbk = d.nph / bk;
+    pl.lev_start = ctx->plan_buf;
+    pl.lev_cell = ctx->plan_buf + nlev + 1;
+    pl.pos_of = ctx->plan_buf + nlev + 1 + bs;
+  }
+  int rc = ensure_buffer(ctx, &ctx->LU, (size_t)NSL * d.N, "block-ILU0 factors");
+  if (rc) return rc;
+  unsigned int nblk = (unsigned int)(ctx->plan.nbi * ctx->plan.nbj * ctx->plan.nbk);
+  if (ctx->op == RKL_OP_CONDUCTION)
+    k_bilu_factor<RKL_OP_CONDUCTION><<<nblk, IB, 0, ctx->stream>>>(d, ctx->plan, ctx->coef, ctx->W, dt, ctx->LU);
+  else
+    k_bilu_factor<RKL_OP_VISCOSITY><<<nblk, IB, 0, ctx->stream>>>(d, ctx->plan, ctx->coef, ctx->W, dt, ctx->LU);
+  rc = cuda_check(ctx, cudaGetLastError(), "block-ILU0 factor launch");
+  if (rc) return rc;
+  ctx->lu_valid = 1;
+  ctx->lu_blk[0] = bi; ctx->lu_blk[1] = bj; ctx->lu_blk[2] = bk;
+  ctx->lu_dt = dt;
+  return RKL_OK;
+}
+
+template <int OP>
+static int pcg_run(rkl_ctx *ctx, double *x, const double *u, const double *x0, double dt, int pc,
+                   double rtol, int maxit, int *iters, double *relres, int *status) {
+  const Dims &d = ctx->d;
+  const long long N = d.N;
+  int rc;
+  if ((rc = ensure_buffer(ctx, &ctx->r, N, "PCG r")) || (rc = ensure_buffer(ctx, &ctx->p, N, "PCG p")) ||
+      (rc = ensure_buffer(ctx, &ctx->y, N, "PCG y")) || (rc = ensure_buffer(ctx, &ctx->zbuf, N, "PCG z")) ||
+      (rc = ensure_buffer(ctx, &ctx->dinv, N, "PCG diag")))
+    return rc;
+  PcgState init{};
+  init.rtol2 = rtol > 0.0 ? rtol * rtol : -1.0;
+  init.maxit = maxit;
+  init.status = PCG_RUNNING;
+  *ctx->h_state = init;
+  if ((rc = cuda_check(ctx, cudaMemcpyAsync(ctx->d_state, ctx->h_state, sizeof(PcgState),
+                                            cudaMemcpyHostToDevice, ctx->stream), "PCG state upload")))
+    return rc;
+  unsigned int g = stride_grid(ctx);
+  const double *xs = x0 ? x0 : u;
+  k_r0<OP><<<g, RB, 0, ctx->stream>>>(d, ctx->coef, ctx->W, dt, u, xs, ctx->r,
+                                      pc == RKL_PC_JACOBI ? ctx->dinv : nullptr, ctx->partials,
+                                      ctx->counter, ctx->d_state);
+  if (x0 && x0 != x) {
+    if ((rc = cuda_check(ctx, cudaMemcpyAsync(x, x0, sizeof(double) * N, cudaMemcpyDeviceToDevice, ctx->stream), "x0 copy")))
+      return rc;
+  }
+  unsigned int nblk = 0;
+  size_t smem = 0;
+  if (pc == RKL_PC_JACOBI) {
+    k_jacobi_init<<<g, RB, 0, ctx->stream>>>(N, ctx->r, ctx->dinv, ctx->p, ctx->partials, ctx->counter, ctx->d_state);
+  } else {
+    nblk = (unsigned int)(ctx->plan.nbi * ctx->plan.nbj * ctx->plan.nbk);
+    smem = sizeof(double) * ctx->plan.bs;
+    k_bilu_apply<OP><<<nblk, IB, smem, ctx->stream>>>(d, ctx->plan, ctx->LU, ctx->r, ctx->zbuf, ctx->partials,
+                                                      ctx->counter, ctx->d_state, 1);
+    k_pupdate_z<<<g, RB, 0, ctx->stream>>>(N, ctx->zbuf, ctx->p, ctx->d_state, 1);
+  }
+  if ((rc = cuda_check(ctx, cudaGetLastError(), "PCG init launch"))) return rc;
+  const int chunk = 8;
+  for (;;) {
+    if ((rc = cuda_check(ctx, cudaMemcpyAsync(ctx->h_state, ctx->d_state, sizeof(PcgState),
+                                              cudaMemcpyDeviceToHost, ctx->stream), "PCG state read")))
+      return rc;
+    if ((rc = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "PCG iteration"))) return rc;
+    const PcgState &h = *ctx->h_state;
+    if (h.status != PCG_RUNNING || h.iters >= maxit) break;
+    for (int q = 0; q < chunk; q++) {
+      k_spmv<OP><<<g, RB, 0, ctx->stream>>>(d, ctx->coef, ctx->W, dt, ctx->p, ctx->y, ctx->partials,
+                                            ctx->counter, ctx->d_state);
+      if (pc == RKL_PC_JACOBI) {
+        k_update_jacobi<<<g, RB, 0, ctx->stream>>>(N, x, ctx->p, ctx->r, ctx->y, ctx->dinv, ctx->partials,
+                                                   ctx->counter, ctx->d_state);
+        k_pupdate_jacobi<<<g, RB, 0, ctx->stream>>>(N, ctx->r, ctx->dinv, ctx->p, ctx->d_state);
+      } else {
+        k_xr_update<<<g, RB, 0, ctx->stream>>>(N, x, ctx->p, ctx->r, ctx->y, ctx->d_state);
+        k_bilu_apply<OP><<<nblk, IB, smem, ctx->stream>>>(d, ctx->plan, ctx->LU, ctx->r, ctx->zbuf,
+                                                          ctx->partials, ctx->counter, ctx->d_state, 0);
+        k_pupdate_z<<<g, RB, 0, ctx->stream>>>(N, ctx->zbuf, ctx->p, ctx->d_state, 0);
+      }
+    }
+    if ((rc = cuda_check(ctx, cudaGetLastError(), "PCG iteration launch"))) return rc;
+  }
+  const PcgState &h = *ctx->h_state;
+  *iters = h.iters;
+  *relres = h.bnorm2 > 0.0 ? std::sqrt(h.rnorm2 / h.bnorm2) : 0.0;
+  int st = h.status;
+  if (st == PCG_RUNNING) st = PCG_MAXIT;  // maxit == 0 without convergence
+  *status = st;
+  return RKL_OK;
+}
+
+int pcg_solve_component(rkl_ctx *ctx, double *x, const double *u, const double *x0, double dt,
+                        int pc, double rtol, int maxit, int *iters, double *relres, int *status) {
+  if (ctx->op == RKL_OP_CONDUCTION)
+    return pcg_run<RKL_OP_CONDUCTION>(ctx, x, u, x0, dt, pc, rtol, maxit, iters, relres, status);
+  return pcg_run<RKL_OP_VISCOSITY>(ctx, x, u, x0, dt, pc, rtol, maxit, iters, relres, status);
+}
+
+}  // namespace rkl

@@ -1,0 +1,111 @@
+// rkl2.cu -- operator apply and the fused stencil + RKL2 stage kernels (Fig. 2).
+//
+// Each stage j >= 2 is one pass over the grid: the stencil of Y_{j-1} and the
+// pointwise recurrence
+//   Y_j = mu_j Y_{j-1} + nu_j Y_{j-2} + (1 - mu_j - nu_j) Y_0
+//         + mu~_j dt M Y_{j-1} + gamma~_j dt M Y_0,      M Y = -W^{-1} S Y,
+// so the stage streams Y_{j-1} (stencil, reused through L1/L2), Y_{j-2}, Y_0, M_0,
+// the 10 stored coefficients and 1/W, and writes Y_j in place of Y_{j-2}.
+// FP64 work per cell: 19 (stencil) + 6 (recurrence) DP instructions.
+#include <cuda_runtime.h>
+
+#include "internal.cuh"
+#include "stencil.cuh"
+
+namespace rkl {
+
+namespace {
+
+constexpr int BLK = 256;
+
+template <int OP>
+__global__ void __launch_bounds__(BLK) k_apply_F(Dims d, const double *__restrict__ coef,
+                                                 const double *__restrict__ invW,
+                                                 const double *__restrict__ u,
+                                                 double *__restrict__ Fu) {
+  long long c = (long long)blockIdx.x * BLK + threadIdx.x;
+  if (c >= d.N) return;
+  int i, j, k;
+  cell_coords(d, c, i, j, k);
+  Nbr n = neighbours(d, i, j, k);
+  Fu[c] = -invW[c] * S_apply<OP>(d, coef, u, c, n);
+}
+
+template <int OP>
+__global__ void __launch_bounds__(BLK) k_stage1(Dims d, const double *__restrict__ coef,
+                                                const double *__restrict__ invW,
+                                                const double *__restrict__ Y0,
+                                                double *__restrict__ M0, double *__restrict__ Y1,
+                                                double mut1dt) {
+  long long c = (long long)blockIdx.x * BLK + threadIdx.x;
+  if (c >= d.N) return;
+  int i, j, k;
+  cell_coords(d, c, i, j, k);
+  Nbr n = neighbours(d, i, j, k);
+  double m0 = -invW[c] * S_apply<OP>(d, coef, Y0, c, n);
+  M0[c] = m0;
+  Y1[c] = fma(mut1dt, m0, Y0[c]);
+}
+
+// Yout may alias Ym2 or Y0 (read and written at the same cell only); never Ym1.
+template <int OP>
+__global__ void __launch_bounds__(BLK) k_stage(Dims d, const double *__restrict__ coef,
+                                               const double *__restrict__ invW,
+                                               const double *__restrict__ Ym1,
+                                               const double *Ym2, const double *Y0,
+                                               const double *__restrict__ M0, double *Yout,
+                                               double mu, double nu, double om, double mutdt,
+                                               double gtdt) {
+  long long c = (long long)blockIdx.x * BLK + threadIdx.x;
+  if (c >= d.N) return;
+  int i, j, k;
+  cell_coords(d, c, i, j, k);
+  Nbr n = neighbours(d, i, j, k);
+  double f = -invW[c] * S_apply<OP>(d, coef, Ym1, c, n);
+  double y = mu * Ym1[c];
+  y = fma(nu, Ym2[c], y);
+  y = fma(om, Y0[c], y);
+  y = fma(mutdt, f, y);
+  y = fma(gtdt, M0[c], y);
+  Yout[c] = y;
+}
+
+}  // namespace
+
+int launch_apply_F(rkl_ctx *ctx, const double *u, double *Fu) {
+  unsigned grid = grid_for(ctx->d.N, BLK);
+  if (ctx->op == RKL_OP_CONDUCTION)
+    k_apply_F<RKL_OP_CONDUCTION><<<grid, BLK, 0, ctx->stream>>>(ctx->d, ctx->coef, ctx->invW, u, Fu);
+  else
+    k_apply_F<RKL_OP_VISCOSITY><<<grid, BLK, 0, ctx->stream>>>(ctx->d, ctx->coef, ctx->invW, u, Fu);
+  return cuda_check(ctx, cudaGetLastError(), "apply_F launch");
+}
+
+int launch_rkl2_stage1(rkl_ctx *ctx, const double *Y0, double *M0, double *Y1, double mut1dt) {
+  unsigned grid = grid_for(ctx->d.N, BLK);
+  if (ctx->op == RKL_OP_CONDUCTION)
+    k_stage1<RKL_OP_CONDUCTION><<<grid, BLK, 0, ctx->stream>>>(ctx->d, ctx->coef, ctx->invW, Y0, M0,
+                                                              Y1, mut1dt);
+  else
+    k_stage1<RKL_OP_VISCOSITY><<<grid, BLK, 0, ctx->stream>>>(ctx->d, ctx->coef, ctx->invW, Y0, M0,
+                                                             Y1, mut1dt);
+  return cuda_check(ctx, cudaGetLastError(), "rkl2 stage-1 launch");
+}
+
+int launch_rkl2_stage(rkl_ctx *ctx, const double *Ym1, const double *Ym2, const double *Y0,
+                      const double *M0, double *Yout, double mu, double nu, double mutdt,
+                      double gtdt) {
+  unsigned grid = grid_for(ctx->d.N, BLK);
+  double om = 1.0 - mu - nu;
+  if (ctx->op == RKL_OP_CONDUCTION)
+    k_stage<RKL_OP_CONDUCTION><<<grid, BLK, 0, ctx->stream>>>(ctx->d, ctx->coef, ctx->invW, Ym1,
+                                                             Ym2, Y0, M0, Yout, mu, nu, om, mutdt,
+                                                             gtdt);
+  else
+    k_stage<RKL_OP_VISCOSITY><<<grid, BLK, 0, ctx->stream>>>(ctx->d, ctx->coef, ctx->invW, Ym1,
+                                                            Ym2, Y0, M0, Yout, mu, nu, om, mutdt,
+                                                            gtdt);
+  return cuda_check(ctx, cudaGetLastError(), "rkl2 stage launch");
+}
+
+}  // namespace rkl

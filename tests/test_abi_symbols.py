@@ -1,0 +1,49 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU and exports every function
+declared in include/*.h; the Python binding wraps exactly those names."""
+import ctypes
+import glob
+import os
+import re
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?\w+\s*\*?\s*(\w+)\s*\(", src, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("rkl_create", "rkl_destroy", "set_coeffs", "apply_F", "rkl2_superstep",
+                     "be_pcg_solve", "rkl2_stage_count", "rkl_strerror"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_1610_01265_gb300 import build as B
+    from paper_1610_01265_gb300 import rklpcg
+
+    path = B.build()
+    lib = ctypes.CDLL(path)
+    for name in declared_functions():
+        assert hasattr(lib, name), f"{name} declared in include/ but not exported"
+    assert set(rklpcg.EXPORTED) == declared_functions()
+
+
+def test_host_only_calls_without_gpu():
+    """Pure host entry points (no device work) answer without a GPU."""
+    from paper_1610_01265_gb300 import rklpcg
+
+    rklpcg.load()
+    assert rklpcg.rkl2_stage_count(100.0) == 20
+    assert rklpcg.rkl2_stage_count(10000.0, rklpcg.RKL_FORCE_ODD) == 201
+    assert rklpcg.strerror(rklpcg.RKL_ENOTCONV).startswith("PCG")
+    lib = rklpcg.load()
+    assert lib.rkl2_stage_count(-1.0, 0) == rklpcg.RKL_EINVAL
+    assert lib.rkl2_stage_count(float("nan"), 0) == rklpcg.RKL_EINVAL
