@@ -1,0 +1,583 @@
+#!/usr/bin/env python
+"""Benchmark of the FP64 hot path on one synthetic coronal grid (128 x 192 x 384 cells).
+
+One step = one pass over every step of the path, through the C ABI:
+  conduction: set_coeffs (+ Gershgorin dt_exp); RKL2 super-steps at dt/dt_exp = 100,
+              1000, 10000 (s = 20, 63, 200); BE+PCG to rtol 1e-10 at the same three
+              dt with point Jacobi and with 8x8x8 block ILU0;
+  viscosity:  set_coeffs; RKL2 at dt/dt_exp = 500 (s = 45) and BE+PCG (Jacobi, block
+              ILU0) at the same dt, on the three Cartesian velocity components.
+Metric: cell-updates/s = cells x (RKL2 stages + PCG iterations, per component) / time.
+
+Timing: W untimed warm-up steps, then K steps between barriers and device syncs, CUDA
+events on the library's stream, max over ranks.  The working set of every stage pass
+(~1.2 GB) is far larger than the 129 MB L2, so no flush is needed between steps.
+Several GPUs (torchrun) run independent replicas (one grid per GPU, no exchange).
+`--impl reference` times the FP64 CPU oracle instead (bounded sample, host cores).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+GRID = (128, 192, 384)
+RATIOS = (100.0, 1000.0, 10000.0)
+VISC_RATIO = 500.0
+RTOL = 1e-10
+MAXIT = 20000
+BLOCK = (8, 8, 8)
+# Algorithmic cost of one fused stencil + RKL2 stage per cell (stored symmetric
+# coefficients): 19 FMA of the stencil, 1/W scaling and 5 recurrence terms = 48 flop;
+# 9 forward coefficients + diagonal + 1/W + Y_{j-1}, Y_{j-2}, Y_0, M_0 read, Y_j written.
+STAGE_FLOP_PER_CELL = 48.0
+STAGE_BYTES_PER_CELL = 128.0
+FP64_PEAK_TFLOPS = 1.25  # nominal FP64 rate of the GB300 (2 DFMA/clk/SM x 152 SMs x 2.07 GHz)
+WORKLOAD = "coronal FP64 conduction+viscosity, 128x192x384 spherical grid"
+
+
+def parse_args():
+    p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-accuracy", action="store_true")
+    p.add_argument("--seed", type=int, default=1)
+    p.add_argument("--profile", choices=("stage", "apply", "pcg-jacobi", "pcg-bilu0", "setup"),
+                   help="run only a minimal case of one kernel family for an ncu capture (no timing)")
+    return p.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def base_config():
+    return {
+        "workload": WORKLOAD,
+        "grid_nr_nth_nph": list(GRID),
+        "cells": GRID[0] * GRID[1] * GRID[2],
+        "rkl2_dt_over_dt_exp": list(RATIOS),
+        "be_dt_over_dt_exp": list(RATIOS),
+        "pcg": ["jacobi", "bilu0-8x8x8"],
+        "rtol": RTOL,
+        "viscosity_dt_over_dt_exp": VISC_RATIO,
+        "l2": "no flush: every stage pass streams ~1.2 GB, far above the 129 MB L2",
+    }
+
+
+# ------------------------------------------------------------------ CPU oracle sample
+def cpu_sample(seed: int):
+    """Bounded sample of the same workload on the FP64 CPU oracle (host cores):
+    4 RKL2 stages + 4 PCG-Jacobi + 4 PCG-block-ILU0 iterations (factorisation included)
+    of the conduction problem on the full grid; operator assembly excluded (set-up)."""
+    import oracle as O
+
+    from paper_1610_01265_gb300 import synth
+
+    nr, nth, nph = GRID
+    c = synth.conduction_case(nr, nth, nph, seed)
+    g = O.Grid(c["rf"], nth, nph)
+    S, W = O.assemble_conduction(g, c["T"], c["bhat"], c["n"])
+    dte, _ = O.gershgorin_dt(g, S, W)
+
+    def run():
+        t0 = time.perf_counter()
+        O.rkl2_superstep(g, S, W, c["T"], 4.0 * dte, 4)
+        O.be_pcg(g, S, W, c["T"], 100 * dte, pc=O.PC_JACOBI, fixed_iters=4)
+        O.be_pcg(g, S, W, c["T"], 100 * dte, pc=O.PC_BILU0, block=BLOCK, fixed_iters=4)
+        return time.perf_counter() - t0
+
+    return run, g.N * 12, O.num_threads()
+
+
+def cpu_sample_text():
+    return ("conduction on the full 128x192x384 grid: one RKL2 super-step of 4 stages, "
+            "4 PCG-Jacobi and 4 PCG-block-ILU0(8^3) iterations (ILU factorisation "
+            "included), operator assembly excluded; cell-updates = cells x 12")
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    run, units, cores = cpu_sample(args.seed)
+    for _ in range(max(args.warmup, 0)):
+        run()
+    times = [run() for _ in range(args.steps)]
+    total = sum(times)
+    value = units * args.steps / total
+    line = {
+        "metric": "cell-updates/s",
+        "value": value,
+        "unit": "cell-updates/s",
+        "n_gpus": args.gpus,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": base_config(),
+        "impl": "reference",
+        "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
+                         "sample": cpu_sample_text()},
+        "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"bench_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.index)], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if not self.proc or not os.path.exists(self.path):
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for name in ("rkl2.cu", "stencil.cuh"):
+        with open(os.path.join(ROOT, "paper_1610_01265_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """Per-launch DRAM bytes of the stage kernel from the committed ncu summary, if it
+    was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "rkl2_stage_128x192x384.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    h = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
+    if not m or not h or h.group(1) != kernel_source_hash():
+        return None
+    return float(m.group(1))
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+class Workload:
+    def __init__(self, R, torch, seed: int, host: bool = False):
+        from paper_1610_01265_gb300 import synth
+
+        self.R, self.torch = R, torch
+        nr, nth, nph = GRID
+        self.N = nr * nth * nph
+        c = synth.conduction_case(nr, nth, nph, seed)
+        v = synth.viscosity_case(nr, nth, nph, seed)
+        self.host = host
+        if host:
+            pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()  # noqa: E731
+            self.T, self.b, self.n = pin(c["T"]), pin(c["bhat"]), pin(c["n"])
+            self.rho, self.nu, self.v = pin(v["rho"]), pin(v["nu"]), pin(v["v"])
+            self.u = pin(np.empty(self.N))
+            self.uv = pin(np.empty(3 * self.N))
+        else:
+            dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
+            self.T, self.b, self.n = dev(c["T"]).view(-1), dev(c["bhat"]).view(-1), dev(c["n"]).view(-1)
+            self.rho, self.nu, self.v = dev(v["rho"]).view(-1), dev(v["nu"]).view(-1), dev(v["v"]).view(-1)
+            self.u = torch.empty_like(self.T)
+            self.uv = torch.empty_like(self.v)
+        self.ctx_c = R.Context(c["rf"], nth, nph)
+        self.ctx_v = R.Context(v["rf"], nth, nph)
+        self.h2d = 0
+        self.d2h = 0
+
+    def _load(self, dst, src):
+        if self.host:
+            np.copyto(dst, src)
+        else:
+            dst.copy_(src)
+
+    def launches(self):
+        return self.ctx_c.kernel_launches + self.ctx_v.kernel_launches
+
+    def step(self, rec=None):
+        """One pass over the hot path; returns (cell-updates, per-path details)."""
+        R, N = self.R, self.N
+        torch = self.torch
+        ev = (lambda: torch.cuda.Event(enable_timing=True)) if rec is not None else None
+        units = 0
+        info = {"rkl2": {}, "be": {}, "visc": {}}
+        self.h2d = self.d2h = 0
+        dte = self.ctx_c.set_conduction(self.T, self.b, self.n)
+        self.h2d += 5 * N * 8
+        for ratio in RATIOS:
+            self._load(self.u, self.T)
+            if ev:
+                e0, e1 = ev(), ev()
+                e0.record()
+            s = self.ctx_c.rkl2_superstep(self.u, ratio * dte, dte)
+            if ev:
+                e1.record()
+                rec.append(("rkl2", s, e0, e1))
+            units += N * s
+            info["rkl2"][str(int(ratio))] = {"s": s}
+            self.h2d += N * 8
+            self.d2h += N * 8
+        for pc, name in ((R.RKL_PC_JACOBI, "jacobi"), (R.RKL_PC_BILU0, "bilu0")):
+            for ratio in RATIOS:
+                self._load(self.u, self.T)
+                code, its, rel = self.ctx_c.be_pcg_solve(self.u, ratio * dte, pc=pc, block=BLOCK, rtol=RTOL,
+                                                         maxit=MAXIT)
+                if code != R.RKL_OK:
+                    raise RuntimeError(f"BE+PCG({name}) at {ratio} did not converge: {R.strerror(code)}")
+                units += N * its[0]
+                info["be"][f"{name}_{int(ratio)}"] = {"iters": its[0], "relres": rel[0]}
+                self.h2d += N * 8
+                self.d2h += N * 8
+        dtv = self.ctx_v.set_viscosity(self.rho, self.nu)
+        self.h2d += 2 * N * 8
+        self._load(self.uv, self.v)
+        s = self.ctx_v.rkl2_superstep(self.uv, VISC_RATIO * dtv, dtv, ncomp=3)
+        units += 3 * N * s
+        info["visc"]["rkl2"] = {"s": s}
+        self.h2d += 3 * N * 8
+        self.d2h += 3 * N * 8
+        for pc, name in ((R.RKL_PC_JACOBI, "jacobi"), (R.RKL_PC_BILU0, "bilu0")):
+            self._load(self.uv, self.v)
+            code, its, rel = self.ctx_v.be_pcg_solve(self.uv, VISC_RATIO * dtv, pc=pc, block=BLOCK, rtol=RTOL,
+                                                     maxit=MAXIT, ncomp=3)
+            if code != R.RKL_OK:
+                raise RuntimeError(f"viscosity BE+PCG({name}) did not converge: {R.strerror(code)}")
+            units += N * sum(its)
+            info["visc"][f"be_{name}"] = {"iters": its, "relres": max(rel)}
+            self.h2d += 3 * N * 8
+            self.d2h += 3 * N * 8
+        info["dt_exp_conduction_s"] = dte
+        info["dt_exp_viscosity_s"] = dtv
+        return units, info
+
+
+def path_timings(wl, torch):
+    """ms per large step of each path (after the timed region, device-resident)."""
+    R = wl.R
+    out = {}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    dte = wl.ctx_c.set_conduction(wl.T, wl.b, wl.n)
+    e0.record()
+    wl.ctx_c.set_conduction(wl.T, wl.b, wl.n)
+    e1.record()
+    torch.cuda.synchronize()
+    out["set_coeffs_conduction_ms"] = e0.elapsed_time(e1)
+    for ratio in RATIOS:
+        wl.u.copy_(wl.T)
+        e0.record()
+        s = wl.ctx_c.rkl2_superstep(wl.u, ratio * dte, dte)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[f"rkl2_{int(ratio)}"] = {"s": s, "ms": ms, "cell_updates_per_s": wl.N * s / ms * 1e3}
+        for pc, name in ((R.RKL_PC_JACOBI, "jacobi"), (R.RKL_PC_BILU0, "bilu0")):
+            wl.u.copy_(wl.T)
+            e0.record()
+            code, its, rel = wl.ctx_c.be_pcg_solve(wl.u, ratio * dte, pc=pc, block=BLOCK, rtol=RTOL, maxit=MAXIT)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            out[f"be_{name}_{int(ratio)}"] = {"iters": its[0], "ms": ms,
+                                              "cell_updates_per_s": wl.N * its[0] / ms * 1e3}
+    return out
+
+
+def accuracy_report(wl, torch):
+    """Relative L2 error of one large step of each method against the semi-discrete
+    solution exp(dt M) T, approximated by 64 RKL2 sub-steps of dt/64 (FP64 GPU path)."""
+    R = wl.R
+    dte = wl.ctx_c.set_conduction(wl.T, wl.b, wl.n)
+    out = {}
+    for ratio in RATIOS:
+        ref = wl.T.clone()
+        for _ in range(64):
+            wl.ctx_c.rkl2_superstep(ref, ratio * dte / 64, dte)
+        nref = torch.linalg.vector_norm(ref - wl.T).item()
+        wl.u.copy_(wl.T)
+        wl.ctx_c.rkl2_superstep(wl.u, ratio * dte, dte)
+        e_rkl = torch.linalg.vector_norm(wl.u - ref).item() / torch.linalg.vector_norm(ref).item()
+        wl.u.copy_(wl.T)
+        wl.ctx_c.be_pcg_solve(wl.u, ratio * dte, pc=R.RKL_PC_BILU0, block=BLOCK, rtol=RTOL, maxit=MAXIT)
+        e_be = torch.linalg.vector_norm(wl.u - ref).item() / torch.linalg.vector_norm(ref).item()
+        out[str(int(ratio))] = {"rkl2_rel_l2": e_rkl, "be_rel_l2": e_be,
+                                "change_rel_l2": nref / torch.linalg.vector_norm(ref).item()}
+    return out
+
+
+def nvtx(name=None):
+    """Push (name) or pop (None) an NVTX range so that an ncu launch list can be limited
+    to the timed region; a no-op where NVTX is unavailable."""
+    try:
+        import torch
+
+        if name is None:
+            torch.cuda.nvtx.range_pop()
+        else:
+            torch.cuda.nvtx.range_push(name)
+    except Exception:
+        pass
+
+
+def profile_case(args):
+    """Minimal device work of one kernel family on the full grid (a few GB), for ncu."""
+    import torch
+
+    from paper_1610_01265_gb300 import build as B
+    from paper_1610_01265_gb300 import rklpcg as R
+    from paper_1610_01265_gb300 import synth
+
+    B.build()
+    nr, nth, nph = GRID
+    c = synth.conduction_case(nr, nth, nph, args.seed)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda().view(-1)  # noqa: E731
+    T, b, n = dev(c["T"]), dev(c["bhat"]), dev(c["n"])
+    ctx = R.Context(c["rf"], nth, nph)
+    dte = ctx.set_conduction(T, b, n)
+    u = T.clone()
+    if args.profile == "stage":
+        ctx.rkl2_superstep(u, 10 * dte, dte, s=4)
+    elif args.profile == "apply":
+        F = torch.empty_like(T)
+        for _ in range(3):
+            ctx.apply_F(T, F)
+    elif args.profile == "pcg-jacobi":
+        ctx.be_pcg_solve(u, 100 * dte, pc=R.RKL_PC_JACOBI, rtol=0.0, maxit=3)
+    elif args.profile == "pcg-bilu0":
+        ctx.be_pcg_solve(u, 100 * dte, pc=R.RKL_PC_BILU0, block=BLOCK, rtol=0.0, maxit=3)
+    elif args.profile == "setup":
+        ctx.set_conduction(T, b, n)
+    torch.cuda.synchronize()
+    ctx.close()
+    print(f"profile case {args.profile} done")
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.profile:
+        return profile_case(args)
+    world, rank, local = dist_env()
+    import torch
+
+    from paper_1610_01265_gb300 import build as B
+    from paper_1610_01265_gb300 import rklpcg as R
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    if rank == 0:
+        B.build()
+    if world > 1:
+        dist.barrier()
+    B.build()
+    R.load()
+
+    # CPU oracle baseline first (rank 0, one GPU only), before any device work
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        run, units, cores = cpu_sample(args.seed)
+        t = run()
+        cpu = {"value": units / t, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
+               "sample": cpu_sample_text(), "seconds": t}
+
+    wl = Workload(R, torch, args.seed + rank)
+    for _ in range(max(args.warmup, 3)):
+        wl.step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    rec = []
+    launches0 = wl.launches()
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        nvtx("timed")
+        t_start.record()
+        units = 0
+        info = None
+        for _ in range(args.steps):
+            u, info = wl.step(rec)
+            units += u
+        t_end.record()
+        torch.cuda.synchronize()
+        nvtx()
+    if world > 1:
+        dist.barrier()
+    launches = wl.launches() - launches0
+    ms = t_start.elapsed_time(t_end)
+    if world > 1:
+        t = torch.tensor([ms, float(units)], dtype=torch.float64, device="cuda")
+        tmax = t[:1].clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        tsum = t[1:].clone()
+        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+        ms, units_all = tmax.item(), tsum.item()
+    else:
+        units_all = float(units)
+    value = units_all / (ms * 1e-3)
+
+    # roofline of the dominant kernel: the fused conduction stencil + RKL2 stage
+    stage_ms = sum(e0.elapsed_time(e1) for _, _, e0, e1 in rec)
+    stages = sum(s for _, s, _, _ in rec)
+    t_stage = stage_ms * 1e-3 / stages
+    flops = STAGE_FLOP_PER_CELL * wl.N
+    achieved_tf = flops / t_stage / 1e12
+    peaks = measured_peaks()
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    roofline = {
+        "kernel": "rkl2 fused stencil+stage (conduction, FP64)",
+        "bound": "alu",
+        "achieved": achieved_tf,
+        "peak": FP64_PEAK_TFLOPS,
+        "unit": "TFLOP/s",
+        "frac": achieved_tf / FP64_PEAK_TFLOPS,
+        "traffic": profiled_traffic(),
+        "launch_ms": t_stage * 1e3,
+        "flop_per_cell": STAGE_FLOP_PER_CELL,
+        "bytes_per_cell": STAGE_BYTES_PER_CELL,
+        "hbm_achieved_gbs": STAGE_BYTES_PER_CELL * wl.N / t_stage / 1e9,
+        "hbm_peak_gbs": hbm_peak,
+        "hbm_frac": STAGE_BYTES_PER_CELL * wl.N / t_stage / 1e9 / hbm_peak,
+        "peak_note": "FP64 peak = recipe nominal 1.25 TFLOP/s; HBM peak = measured copy (MEASURED_PEAKS.json)",
+    }
+
+    detail = {"last_step": info}
+    if rank == 0:
+        detail["paths"] = path_timings(wl, torch)
+        if not args.no_accuracy:
+            detail["accuracy_vs_semidiscrete"] = accuracy_report(wl, torch)
+
+    e2e = None
+    if not args.no_e2e:
+        hw = Workload(R, torch, args.seed + rank, host=True)
+        hw.step()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        eu = 0
+        for _ in range(args.steps):
+            u, _ = hw.step()
+            eu += u
+        torch.cuda.synchronize()
+        et = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([et, float(eu)], dtype=torch.float64, device="cuda")
+            a, b = t[:1].clone(), t[1:].clone()
+            dist.all_reduce(a, op=dist.ReduceOp.MAX)
+            dist.all_reduce(b, op=dist.ReduceOp.SUM)
+            et, eu = a.item(), b.item()
+        e2e = {"value": eu / et, "unit": "cell-updates/s", "h2d_bytes_per_step": hw.h2d,
+               "d2h_bytes_per_step": hw.d2h}
+
+    if rank == 0:
+        line = {
+            "metric": "cell-updates/s",
+            "value": value,
+            "unit": "cell-updates/s",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": max(args.warmup, 3),
+            "ms_per_step": ms / args.steps,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f64",
+            "data": "synthetic",
+            "config": base_config(),
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+            "detail": detail,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

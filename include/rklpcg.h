@@ -81,6 +81,11 @@ int rkl_set_stream(rkl_ctx *ctx, void *cuda_stream);
 const char *rkl_strerror(int code);
 const char *rkl_last_error(const rkl_ctx *ctx);
 
+/* Number of CUDA kernels this context has launched since rkl_create (instrumentation:
+ * every launch of every entry point is counted, including PCG iterations queued after
+ * convergence that return at once).  -1 for a NULL context.  No paper counterpart. */
+long long rkl_kernel_launches(const rkl_ctx *ctx);
+
 /* Eq. 5 (Sec. 3): number of RKL2 stages for dt/dt_exp, read as
  * s = ceil((sqrt(9 + 16 dt/dt_exp) - 1) / 2), at least 2, odd with RKL_FORCE_ODD.
  * Returns s, or RKL_EINVAL for a non-positive or non-finite ratio. */

@@ -98,20 +98,26 @@ bool is_device_ptr(const void *p) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-// Staging arena for host arrays: returns a device view of n doubles at slot offset.
-int stage_view(rkl_ctx *ctx, size_t offset, size_t n, double **out) {
-  size_t need = offset + n;
-  if (need > ctx->stage_cap) {
-    if (ctx->stage) {
-      cudaStreamSynchronize(ctx->stream);
-      cudaFree(ctx->stage);
-      ctx->stage = nullptr;
-      ctx->stage_cap = 0;
-    }
-    int rc = cuda_check(ctx, cudaMalloc(&ctx->stage, need * sizeof(double)), "alloc staging");
+// Staging arena for host arrays.  Every entry point sizes the arena for all of its
+// arguments (ensure_stage) before staging the first one, so that a view handed out
+// for one argument is never invalidated by a reallocation for the next.
+int ensure_stage(rkl_ctx *ctx, size_t need) {
+  if (need <= ctx->stage_cap) return RKL_OK;
+  if (ctx->stage) {
+    int rc = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "staging resize");
     if (rc) return rc;
-    ctx->stage_cap = need;
+    cudaFree(ctx->stage);
+    ctx->stage = nullptr;
+    ctx->stage_cap = 0;
   }
+  int rc = cuda_check(ctx, cudaMalloc(&ctx->stage, need * sizeof(double)), "alloc staging");
+  if (rc) return rc;
+  ctx->stage_cap = need;
+  return RKL_OK;
+}
+
+int stage_view(rkl_ctx *ctx, size_t offset, size_t n, double **out) {
+  if (offset + n > ctx->stage_cap) return set_error(ctx, RKL_ECUDA, "internal: staging arena too small");
   *out = ctx->stage + offset;
   return RKL_OK;
 }
@@ -162,6 +168,8 @@ const char *rkl_strerror(int code) {
 }
 
 const char *rkl_last_error(const rkl_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+long long rkl_kernel_launches(const rkl_ctx *ctx) { return ctx ? ctx->launches : -1; }
 
 int rkl2_stage_count(double ratio, int flags) {
   if (!(std::isfinite(ratio) && ratio > 0.0)) return RKL_EINVAL;
@@ -255,6 +263,8 @@ int set_coeffs(rkl_ctx *ctx, int op, const double *a, const double *b, const dou
   if (rc) return rc;
   double *da, *db = nullptr, *dc;
   bool sa, sb = false, sc;
+  if (!is_device_ptr(a) || (b && !is_device_ptr(b)) || !is_device_ptr(c))
+    if ((rc = ensure_stage(ctx, 5 * N))) return rc;
   if ((rc = to_device(ctx, a, N, 0, true, &da, &sa))) return rc;
   if (op == RKL_OP_CONDUCTION && (rc = to_device(ctx, b, 3 * N, N, true, &db, &sb))) return rc;
   if ((rc = to_device(ctx, c, N, 4 * N, true, &dc, &sc))) return rc;
@@ -299,6 +309,8 @@ int apply_F(rkl_ctx *ctx, const double *u, double *Fu, int ncomp) {
   double *du, *dF;
   bool su, sF;
   int rc;
+  if (!is_device_ptr(u) || !is_device_ptr(Fu))
+    if ((rc = ensure_stage(ctx, 2 * tot))) return rc;
   if ((rc = to_device(ctx, u, tot, 0, true, &du, &su))) return rc;
   if ((rc = to_device(ctx, Fu, tot, tot, false, &dF, &sF))) return rc;
   for (int q = 0; q < ncomp; q++)
@@ -326,6 +338,7 @@ int rkl2_superstep(rkl_ctx *ctx, double *u, int ncomp, double dt, double dt_exp,
     return rc;
   double *du;
   bool su;
+  if (!is_device_ptr(u) && (rc = ensure_stage(ctx, tot))) return rc;
   if ((rc = to_device(ctx, u, tot, 0, true, &du, &su))) return rc;
   const double w1 = 4.0 / ((double)s * s + s - 2.0);
   for (int q = 0; q < ncomp; q++) {
@@ -381,6 +394,8 @@ int be_pcg_solve(rkl_ctx *ctx, double *u, int ncomp, double dt, int pc, const in
   const size_t N = (size_t)ctx->d.N, tot = N * ncomp;
   double *du, *dx0 = nullptr;
   bool su, sx = false;
+  if (!is_device_ptr(u) || (x0 && !is_device_ptr(x0)))
+    if ((rc = ensure_stage(ctx, 2 * tot))) return rc;
   if ((rc = to_device(ctx, u, tot, 0, true, &du, &su))) return rc;
   if (x0 && (rc = to_device(ctx, x0, tot, tot, true, &dx0, &sx))) return rc;
   int worst = RKL_OK;

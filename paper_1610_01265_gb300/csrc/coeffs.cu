@@ -299,6 +299,7 @@ int launch_setup_conduction(rkl_ctx *ctx, const double *T, const double *bhat, c
   k_faces_cond<<<grid, BLK, 0, ctx->stream>>>(d, ctx->geo, bhat, kappa, FS);
   k_assemble_cond<<<grid, BLK, 0, ctx->stream>>>(d, ctx->geo, FS, ctx->invW, ctx->coef,
                                                 ctx->d_lammax, ctx->d_flag);
+  ctx->launches += 3;
   return cuda_check(ctx, cudaGetLastError(), "set_coeffs(conduction) launch");
 }
 
@@ -310,6 +311,7 @@ int launch_setup_viscosity(rkl_ctx *ctx, const double *rho, const double *nu) {
                                             ctx->d_flag);
   k_assemble_visc<<<grid, BLK, 0, ctx->stream>>>(d, ctx->geo, mu, ctx->invW, ctx->coef,
                                                 ctx->d_lammax, ctx->d_flag);
+  ctx->launches += 2;
   return cuda_check(ctx, cudaGetLastError(), "set_coeffs(viscosity) launch");
 }
 

@@ -126,6 +126,9 @@ struct rkl_ctx {
   double lu_dt = 0.0;
   int lu_valid = 0;
 
+  // number of kernels this context has launched (all entry points)
+  long long launches = 0;
+
   // host-pointer staging
   double *stage = nullptr;
   size_t stage_cap = 0;  // doubles

@@ -394,7 +394,11 @@ int bilu0_prepare(rkl_ctx *ctx, const int *block, double dt) {
           cell[p] = l;
           pos[l] = p;
         }
-    if (ctx->plan_buf) cudaFree(ctx->plan_buf);
+    if (ctx->plan_buf) {
+      int rc0 = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "ILU plan resize");
+      if (rc0) return rc0;
+      cudaFree(ctx->plan_buf);
+    }
     ctx->plan_buf = nullptr;
     size_t nint = (size_t)(nlev + 1) + 2 * (size_t)bs;
     if (cuda_check(ctx, cudaMalloc(&ctx->plan_buf, nint * sizeof(int)), "alloc ILU plan")) return RKL_ENOMEM;
@@ -422,6 +426,7 @@ int bilu0_prepare(rkl_ctx *ctx, const int *block, double dt) {
     k_bilu_factor<RKL_OP_CONDUCTION><<<nblk, IB, 0, ctx->stream>>>(d, ctx->plan, ctx->coef, ctx->W, dt, ctx->LU);
   else
     k_bilu_factor<RKL_OP_VISCOSITY><<<nblk, IB, 0, ctx->stream>>>(d, ctx->plan, ctx->coef, ctx->W, dt, ctx->LU);
+  ctx->launches += 1;
   rc = cuda_check(ctx, cudaGetLastError(), "block-ILU0 factor launch");
   if (rc) return rc;
   ctx->lu_valid = 1;
@@ -468,6 +473,7 @@ static int pcg_run(rkl_ctx *ctx, double *x, const double *u, const double *x0, d
                                                       ctx->counter, ctx->d_state, 1);
     k_pupdate_z<<<g, RB, 0, ctx->stream>>>(N, ctx->zbuf, ctx->p, ctx->d_state, 1);
   }
+  ctx->launches += 2;
   if ((rc = cuda_check(ctx, cudaGetLastError(), "PCG init launch"))) return rc;
   const int chunk = 8;
   for (;;) {
@@ -491,6 +497,7 @@ static int pcg_run(rkl_ctx *ctx, double *x, const double *u, const double *x0, d
         k_pupdate_z<<<g, RB, 0, ctx->stream>>>(N, ctx->zbuf, ctx->p, ctx->d_state, 0);
       }
     }
+    ctx->launches += (long long)chunk * (pc == RKL_PC_JACOBI ? 3 : 4);
     if ((rc = cuda_check(ctx, cudaGetLastError(), "PCG iteration launch"))) return rc;
   }
   const PcgState &h = *ctx->h_state;

@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(BLK) k_apply_F(Dims d, const double *__restric
 }
 
 template <int OP>
-__global__ void __launch_bounds__(BLK) k_stage1(Dims d, const double *__restrict__ coef,
+__global__ void __launch_bounds__(BLK) k_rkl2_first(Dims d, const double *__restrict__ coef,
                                                 const double *__restrict__ invW,
                                                 const double *__restrict__ Y0,
                                                 double *__restrict__ M0, double *__restrict__ Y1,
@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(BLK) k_stage1(Dims d, const double *__restrict
 
 // Yout may alias Ym2 or Y0 (read and written at the same cell only); never Ym1.
 template <int OP>
-__global__ void __launch_bounds__(BLK) k_stage(Dims d, const double *__restrict__ coef,
+__global__ void __launch_bounds__(BLK) k_rkl2_stage(Dims d, const double *__restrict__ coef,
                                                const double *__restrict__ invW,
                                                const double *__restrict__ Ym1,
                                                const double *Ym2, const double *Y0,
@@ -78,17 +78,19 @@ int launch_apply_F(rkl_ctx *ctx, const double *u, double *Fu) {
     k_apply_F<RKL_OP_CONDUCTION><<<grid, BLK, 0, ctx->stream>>>(ctx->d, ctx->coef, ctx->invW, u, Fu);
   else
     k_apply_F<RKL_OP_VISCOSITY><<<grid, BLK, 0, ctx->stream>>>(ctx->d, ctx->coef, ctx->invW, u, Fu);
+  ctx->launches += 1;
   return cuda_check(ctx, cudaGetLastError(), "apply_F launch");
 }
 
 int launch_rkl2_stage1(rkl_ctx *ctx, const double *Y0, double *M0, double *Y1, double mut1dt) {
   unsigned grid = grid_for(ctx->d.N, BLK);
   if (ctx->op == RKL_OP_CONDUCTION)
-    k_stage1<RKL_OP_CONDUCTION><<<grid, BLK, 0, ctx->stream>>>(ctx->d, ctx->coef, ctx->invW, Y0, M0,
+    k_rkl2_first<RKL_OP_CONDUCTION><<<grid, BLK, 0, ctx->stream>>>(ctx->d, ctx->coef, ctx->invW, Y0, M0,
                                                               Y1, mut1dt);
   else
-    k_stage1<RKL_OP_VISCOSITY><<<grid, BLK, 0, ctx->stream>>>(ctx->d, ctx->coef, ctx->invW, Y0, M0,
+    k_rkl2_first<RKL_OP_VISCOSITY><<<grid, BLK, 0, ctx->stream>>>(ctx->d, ctx->coef, ctx->invW, Y0, M0,
                                                              Y1, mut1dt);
+  ctx->launches += 1;
   return cuda_check(ctx, cudaGetLastError(), "rkl2 stage-1 launch");
 }
 
@@ -98,13 +100,14 @@ int launch_rkl2_stage(rkl_ctx *ctx, const double *Ym1, const double *Ym2, const 
   unsigned grid = grid_for(ctx->d.N, BLK);
   double om = 1.0 - mu - nu;
   if (ctx->op == RKL_OP_CONDUCTION)
-    k_stage<RKL_OP_CONDUCTION><<<grid, BLK, 0, ctx->stream>>>(ctx->d, ctx->coef, ctx->invW, Ym1,
+    k_rkl2_stage<RKL_OP_CONDUCTION><<<grid, BLK, 0, ctx->stream>>>(ctx->d, ctx->coef, ctx->invW, Ym1,
                                                              Ym2, Y0, M0, Yout, mu, nu, om, mutdt,
                                                              gtdt);
   else
-    k_stage<RKL_OP_VISCOSITY><<<grid, BLK, 0, ctx->stream>>>(ctx->d, ctx->coef, ctx->invW, Ym1,
+    k_rkl2_stage<RKL_OP_VISCOSITY><<<grid, BLK, 0, ctx->stream>>>(ctx->d, ctx->coef, ctx->invW, Ym1,
                                                             Ym2, Y0, M0, Yout, mu, nu, om, mutdt,
                                                             gtdt);
+  ctx->launches += 1;
   return cuda_check(ctx, cudaGetLastError(), "rkl2 stage launch");
 }
 

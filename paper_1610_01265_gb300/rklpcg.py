@@ -33,7 +33,8 @@ RKL_BETA_TCUT = 1
 RKL_FORCE_ODD = 1
 
 EXPORTED = ("rkl_create", "rkl_destroy", "rkl_set_stream", "rkl_strerror", "rkl_last_error",
-            "rkl2_stage_count", "set_coeffs", "apply_F", "rkl2_superstep", "be_pcg_solve")
+            "rkl_kernel_launches", "rkl2_stage_count", "set_coeffs", "apply_F", "rkl2_superstep",
+            "be_pcg_solve")
 
 
 class RklError(RuntimeError):
@@ -74,6 +75,8 @@ def load(path: str | None = None):
     lib.rkl_strerror.restype = ctypes.c_char_p
     lib.rkl_last_error.argtypes = [P]
     lib.rkl_last_error.restype = ctypes.c_char_p
+    lib.rkl_kernel_launches.argtypes = [P]
+    lib.rkl_kernel_launches.restype = ctypes.c_longlong
     lib.rkl2_stage_count.argtypes = [D, I]
     lib.set_coeffs.argtypes = [P, I, P, P, P, D, I, ctypes.POINTER(D)]
     lib.apply_F.argtypes = [P, P, P, I]
@@ -171,6 +174,10 @@ class Context:
     def _check(self, code: int, where: str):
         if code != RKL_OK:
             raise RklError(code, where, self._lib.rkl_last_error(self._h).decode())
+
+    @property
+    def kernel_launches(self) -> int:
+        return int(self._lib.rkl_kernel_launches(self._h))
 
     def set_stream(self, stream):
         self._check(self._lib.rkl_set_stream(self._h, stream), "rkl_set_stream")

@@ -13,7 +13,7 @@ def declared_functions():
     for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
         src = open(h).read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-        for m in re.finditer(r"^\s*(?:const\s+)?\w+\s*\*?\s*(\w+)\s*\(", src, flags=re.M):
+        for m in re.finditer(r"^[A-Za-z_](?:[\w ]*?[\s\*])(\w+)\s*\(", src, flags=re.M):
             names.add(m.group(1))
     return names
 

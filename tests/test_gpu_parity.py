@@ -37,7 +37,7 @@ def torch_cuda():
 
 
 def dev(torch, a):
-    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+    return torch.from_numpy(np.array(a, dtype=np.float64, order="C")).cuda()
 
 
 def host(t):
@@ -138,7 +138,8 @@ def test_rkl2_viscosity_three_components(oracle_mod, R, torch_cuda):
         assert rel_l2(out[q], ref) <= 1e-12
 
 
-@pytest.mark.parametrize("pc,block", [(1, (8, 8, 8)), (2, (8, 8, 8)), (2, (4, 4, 4)), (2, (2, 3, 4))])
+@pytest.mark.parametrize("pc,block", [(1, (8, 8, 8)), (2, (4, 6, 8)), (2, (4, 4, 4)), (2, (2, 3, 4)),
+                                      (2, (16, 1, 1)), (2, (1, 1, 1))])
 @pytest.mark.parametrize("ratio", [100.0, 10000.0])
 def test_be_pcg_fixed_iterations(oracle_mod, R, torch_cuda, pc, block, ratio):
     """Same number of CG iterations on both sides (rtol <= 0 runs exactly maxit)."""
@@ -211,6 +212,30 @@ def test_host_pointers_match_device(oracle_mod, R, torch_cuda):
     code, its, rel = ctx.be_pcg_solve(u, 300 * dte, pc=2, block=(4, 4, 4), rtol=0.0, maxit=9)
     x, *_ = O.be_pcg(g, S, W, c["T"], 300 * dte, pc=2, block=(4, 4, 4), fixed_iters=9)
     assert rel_l2(u, x) <= 1e-12
+
+
+def test_host_staging_grows_across_calls(oracle_mod, R, torch_cuda):
+    """Host-pointer calls whose staging needs grow from call to call (N, then 5N for the
+    coefficients, then 2N): every argument keeps a valid staged copy."""
+    O = oracle_mod
+    dims = (24, 16, 32)
+    c = synth.conduction_case(*dims, seed=4)
+    g = O.Grid(c["rf"], dims[1], dims[2])
+    S, W = O.assemble_conduction(g, c["T"], c["bhat"], c["n"])
+    dte_o, _ = O.gershgorin_dt(g, S, W)
+    ctx = R.Context(c["rf"], dims[1], dims[2])
+    with pytest.raises(R.RklError):
+        ctx.rkl2_superstep(c["T"].copy(), 1.0, 1.0)  # before set_coeffs: state error
+    dte = ctx.set_conduction(c["T"], c["bhat"], c["n"])
+    assert dte == pytest.approx(dte_o, rel=1e-13)
+    u = c["T"].copy()
+    ctx.rkl2_superstep(u, 50 * dte, dte, s=12)
+    assert rel_l2(u, O.rkl2_superstep(g, S, W, c["T"], 50 * dte, 12)) <= 1e-12
+    dte = ctx.set_conduction(c["T"], c["bhat"], c["n"])
+    Fu = np.empty(g.N)
+    ctx.apply_F(c["T"], Fu)
+    check_F(O, g, S, W, c["T"], Fu.reshape(g.shape))
+    ctx.close()
 
 
 def test_error_paths(R, torch_cuda):
