@@ -243,13 +243,13 @@ class Workload:
         v = synth.viscosity_case(nr, nth, nph, seed)
         self.host = host
         if host:
-            pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()  # noqa: E731
+            pin = lambda a: torch.from_numpy(np.array(a, dtype=np.float64).reshape(-1)).pin_memory().numpy()  # noqa: E731
             self.T, self.b, self.n = pin(c["T"]), pin(c["bhat"]), pin(c["n"])
             self.rho, self.nu, self.v = pin(v["rho"]), pin(v["nu"]), pin(v["v"])
             self.u = pin(np.empty(self.N))
             self.uv = pin(np.empty(3 * self.N))
         else:
-            dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
+            dev = lambda a: torch.from_numpy(np.array(a, dtype=np.float64)).cuda()  # noqa: E731
             self.T, self.b, self.n = dev(c["T"]).view(-1), dev(c["bhat"]).view(-1), dev(c["n"]).view(-1)
             self.rho, self.nu, self.v = dev(v["rho"]).view(-1), dev(v["nu"]).view(-1), dev(v["v"]).view(-1)
             self.u = torch.empty_like(self.T)
@@ -403,7 +403,7 @@ def profile_case(args):
     B.build()
     nr, nth, nph = GRID
     c = synth.conduction_case(nr, nth, nph, args.seed)
-    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda().view(-1)  # noqa: E731
+    dev = lambda a: torch.from_numpy(np.array(a, dtype=np.float64)).cuda().view(-1)  # noqa: E731
     T, b, n = dev(c["T"]), dev(c["bhat"]), dev(c["n"])
     ctx = R.Context(c["rf"], nth, nph)
     dte = ctx.set_conduction(T, b, n)

@@ -189,7 +189,7 @@ def viscosity_case(nr: int, nth: int, nph: int, seed: int = 1) -> dict:
         "shape": (nph, nth, nr),
         "rf": rf,
         "rho": np.ascontiguousarray(rho, dtype=np.float64),
-        "nu": np.ascontiguousarray(np.broadcast_to(nu, (nph, nth, nr)), dtype=np.float64),
+        "nu": np.array(np.broadcast_to(nu, (nph, nth, nr)), dtype=np.float64),
         "v": np.ascontiguousarray(v, dtype=np.float64),
     }
 
