@@ -73,15 +73,20 @@ struct PcgState {
 
 enum { PCG_RUNNING = 0, PCG_CONVERGED = 1, PCG_BREAKDOWN = 2, PCG_MAXIT = 3 };
 
-// block-ILU0 level schedule of one block shape (device pointers)
+// block-ILU0 level schedule of one block shape (device pointers).  G blocks are
+// solved together by one CTA; their factors are stored group by group as
+// [slot][G * bs] with the cells of one wavefront of all G blocks contiguous.
 struct IluPlan {
   int bi, bj, bk, bs;     // block dims and cells per block
   int nlev;               // number of wavefront levels
   int nbi, nbj, nbk;      // blocks along r, theta, phi
+  int nblocks, G, ngroups;
   const int *lev_start;   // [nlev+1] offsets into lev_cell
   const int *lev_cell;    // [bs] block-local index (li + bi*(lj + bj*lk)) in level order
   const int *pos_of;      // [bs] level-order position of a block-local index
 };
+
+enum { ILU_SLOTS = 20 };  // 0 U_ii, 1..9 L (lower), 10..18 U (upper), 19 1/U_ii
 
 }  // namespace rkl
 
@@ -120,6 +125,7 @@ struct rkl_ctx {
 
   // block ILU0
   double *LU = nullptr;
+  size_t lu_cap = 0;  // doubles
   int *plan_buf = nullptr;
   rkl::IluPlan plan{};
   int lu_blk[3] = {0, 0, 0};

@@ -26,7 +26,6 @@ namespace rkl {
 namespace {
 
 constexpr int RB = 256;   // block size of grid-stride reduction kernels
-constexpr int IB = 64;    // block size of the block-ILU0 kernels
 constexpr int NSL = 19;   // slots of an ILU row: 0 diag, 1+m = -FWD[m], 10+m = +FWD[m]
 
 __device__ __forceinline__ int slot_di(int s) { return s == 0 ? 0 : (s < 10 ? -fwd_di(s - 1) : fwd_di(s - 10)); }
@@ -226,18 +225,19 @@ __global__ void __launch_bounds__(RB) k_pupdate_z(long long N, const double *__r
 
 // ---------------- block ILU0 ----------------
 
+constexpr int GB = 256;  // threads of a block-ILU0 CTA (G blocks per CTA)
+
 struct BlockCell {
-  int l, li, lj, lk;
+  int li, lj, lk;
   long long c;
 };
 
-__device__ __forceinline__ BlockCell block_cell(const Dims &d, const IluPlan &pl, int blk, int p) {
+__device__ __forceinline__ BlockCell block_cell(const Dims &d, const IluPlan &pl, int blk, int l) {
   BlockCell b;
   int bI = blk % pl.nbi, bJ = (blk / pl.nbi) % pl.nbj, bK = blk / (pl.nbi * pl.nbj);
-  b.l = pl.lev_cell[p];
-  b.li = b.l % pl.bi;
-  b.lj = (b.l / pl.bi) % pl.bj;
-  b.lk = b.l / (pl.bi * pl.bj);
+  b.li = l % pl.bi;
+  b.lj = (l / pl.bi) % pl.bj;
+  b.lk = l / (pl.bi * pl.bj);
   int i = bI * pl.bi + b.li, j = bJ * pl.bj + b.lj, k = bK * pl.bk + b.lk;
   b.c = ((long long)k * d.nth + j) * d.nr + i;
   return b;
@@ -268,18 +268,32 @@ __device__ __forceinline__ int slot_of_offset(int di, int dj, int dk) {
   return -1;
 }
 
-// zero-fill IKJ ILU of each block's rows of A = W + dt S (App. A)
+// position inside a group's [G * bs] slot array of block bb's local cell l
+__device__ __forceinline__ int group_pos(const IluPlan &pl, int bb, int l) {
+  int li = l % pl.bi, lj = (l / pl.bi) % pl.bj, lk = l / (pl.bi * pl.bj);
+  int lev = li + 2 * lj + 3 * lk;
+  int ls = pl.lev_start[lev], nl = pl.lev_start[lev + 1] - ls;
+  return pl.G * ls + bb * nl + (pl.pos_of[l] - ls);
+}
+
+// zero-fill IKJ ILU of the rows of A = W + dt S of G blocks (App. A), wavefront by
+// wavefront; rows of earlier wavefronts are read back from the group's factor array.
 template <int OP>
-__global__ void __launch_bounds__(IB) k_bilu_factor(Dims d, IluPlan pl,
+__global__ void __launch_bounds__(GB) k_bilu_factor(Dims d, IluPlan pl,
                                                     const double *__restrict__ coef,
                                                     const double *__restrict__ W, double dt,
                                                     double *__restrict__ LU) {
-  const int blk = blockIdx.x;
-  const size_t base = (size_t)blk * NSL * pl.bs;
+  const int grp = blockIdx.x, b0 = grp * pl.G;
+  const int gcount = min(pl.G, pl.nblocks - b0);
+  const size_t gs = (size_t)pl.G * pl.bs;
+  double *LUg = LU + (size_t)grp * ILU_SLOTS * gs;
   const int nf = OP == RKL_OP_CONDUCTION ? 9 : 3;
   for (int lev = 0; lev < pl.nlev; lev++) {
-    for (int p = pl.lev_start[lev] + threadIdx.x; p < pl.lev_start[lev + 1]; p += IB) {
-      BlockCell b = block_cell(d, pl, blk, p);
+    const int ls = pl.lev_start[lev], nl = pl.lev_start[lev + 1] - ls;
+    for (int q = threadIdx.x; q < gcount * nl; q += GB) {
+      const int bb = q / nl, l = pl.lev_cell[ls + (q - bb * nl)];
+      const size_t p = (size_t)pl.G * ls + q;
+      BlockCell b = block_cell(d, pl, b0 + bb, l);
       double a[NSL];
       a[0] = fma(dt, S_diag<OP>(d, coef, b.c), W[b.c]);
       for (int m = 0; m < 9; m++) {
@@ -293,73 +307,90 @@ __global__ void __launch_bounds__(IB) k_bilu_factor(Dims d, IluPlan pl,
       // lower slots in increasing order of the neighbour's position (lexicographic)
       for (int rk = 0; rk < 13; rk++) {
         int s = -1;
-        for (int q = 1; q < 10; q++)
-          if (lex_rank(q) == rk) s = q;
+        for (int q2 = 1; q2 < 10; q2++)
+          if (lex_rank(q2) == rk) s = q2;
         if (s < 0 || !in_pattern<OP>(pl, b, s)) continue;
-        int kpos = pl.pos_of[b.l + slot_ldelta(pl, s)];
-        double L = a[s] / LU[base + kpos];
+        const int kp = group_pos(pl, bb, l + slot_ldelta(pl, s));
+        const double L = a[s] / LUg[kp];
         a[s] = L;
-        for (int q = 0; q < NSL; q++) {
-          if (lex_rank(q) <= rk || !in_pattern<OP>(pl, b, q)) continue;
-          int s3 = slot_of_offset(slot_di(q) - slot_di(s), slot_dj(q) - slot_dj(s),
-                                  slot_dk(q) - slot_dk(s));
+        for (int q2 = 0; q2 < NSL; q2++) {
+          if (lex_rank(q2) <= rk || !in_pattern<OP>(pl, b, q2)) continue;
+          int s3 = slot_of_offset(slot_di(q2) - slot_di(s), slot_dj(q2) - slot_dj(s),
+                                  slot_dk(q2) - slot_dk(s));
           if (s3 < 0) continue;
-          // (k, j) must be in row k's pattern; j = this row's neighbour q is in the block
           if (OP == RKL_OP_VISCOSITY && s3 != 0 && (((s3 - 1) % 9) >= 3)) continue;
-          a[q] -= L * LU[base + (size_t)s3 * pl.bs + kpos];
+          a[q2] -= L * LUg[(size_t)s3 * gs + kp];
         }
       }
-      for (int q = 0; q < NSL; q++)
-        LU[base + (size_t)q * pl.bs + p] = in_pattern<OP>(pl, b, q) ? a[q] : 0.0;
+      for (int q2 = 0; q2 < NSL; q2++)
+        LUg[(size_t)q2 * gs + p] = in_pattern<OP>(pl, b, q2) ? a[q2] : 0.0;
+      LUg[(size_t)(ILU_SLOTS - 1) * gs + p] = 1.0 / a[0];
     }
     __syncthreads();
   }
 }
 
-// z = (LU)^{-1} r on every block (forward unit-L, backward U), then r.z and r.r
+// z = (LU)^{-1} r on G blocks: residual staged in shared memory, forward (unit L) and
+// backward (U, times 1/U_ii) sweeps wavefront by wavefront, then r.z and r.r
 template <int OP>
-__global__ void __launch_bounds__(IB) k_bilu_apply(Dims d, IluPlan pl,
+__global__ void __launch_bounds__(GB) k_bilu_apply(Dims d, IluPlan pl,
                                                    const double *__restrict__ LU,
                                                    const double *__restrict__ r,
                                                    double *__restrict__ z, double *partials,
                                                    unsigned int *counter, PcgState *st,
                                                    int init) {
   if (!init && st->status != PCG_RUNNING) return;
-  extern __shared__ double zs[];
-  const int blk = blockIdx.x;
-  const size_t base = (size_t)blk * NSL * pl.bs;
+  extern __shared__ double zs[];  // [G][bs]
+  const int grp = blockIdx.x, b0 = grp * pl.G;
+  const int gcount = min(pl.G, pl.nblocks - b0);
+  const size_t gs = (size_t)pl.G * pl.bs;
+  const double *LUg = LU + (size_t)grp * ILU_SLOTS * gs;
+  for (int q = threadIdx.x; q < gcount * pl.bs; q += GB) {
+    const int bb = q / pl.bs, l = q - bb * pl.bs;
+    zs[q] = r[block_cell(d, pl, b0 + bb, l).c];
+  }
+  __syncthreads();
   for (int lev = 0; lev < pl.nlev; lev++) {
-    for (int p = pl.lev_start[lev] + threadIdx.x; p < pl.lev_start[lev + 1]; p += IB) {
-      BlockCell b = block_cell(d, pl, blk, p);
-      double v = r[b.c];
+    const int ls = pl.lev_start[lev], nl = pl.lev_start[lev + 1] - ls;
+    for (int q = threadIdx.x; q < gcount * nl; q += GB) {
+      const int bb = q / nl, l = pl.lev_cell[ls + (q - bb * nl)];
+      const size_t p = (size_t)pl.G * ls + q;
+      BlockCell b = block_cell(d, pl, b0 + bb, l);
+      double *zb = zs + bb * pl.bs;
+      double v = zb[l];
 #pragma unroll
       for (int s = 1; s < 10; s++)
-        if (in_pattern<OP>(pl, b, s)) v = fma(-LU[base + (size_t)s * pl.bs + p], zs[b.l + slot_ldelta(pl, s)], v);
-      zs[b.l] = v;
+        if (in_pattern<OP>(pl, b, s)) v = fma(-LUg[(size_t)s * gs + p], zb[l + slot_ldelta(pl, s)], v);
+      zb[l] = v;
     }
     __syncthreads();
   }
   for (int lev = pl.nlev - 1; lev >= 0; lev--) {
-    for (int p = pl.lev_start[lev] + threadIdx.x; p < pl.lev_start[lev + 1]; p += IB) {
-      BlockCell b = block_cell(d, pl, blk, p);
-      double v = zs[b.l];
+    const int ls = pl.lev_start[lev], nl = pl.lev_start[lev + 1] - ls;
+    for (int q = threadIdx.x; q < gcount * nl; q += GB) {
+      const int bb = q / nl, l = pl.lev_cell[ls + (q - bb * nl)];
+      const size_t p = (size_t)pl.G * ls + q;
+      BlockCell b = block_cell(d, pl, b0 + bb, l);
+      double *zb = zs + bb * pl.bs;
+      double v = zb[l];
 #pragma unroll
       for (int s = 10; s < NSL; s++)
-        if (in_pattern<OP>(pl, b, s)) v = fma(-LU[base + (size_t)s * pl.bs + p], zs[b.l + slot_ldelta(pl, s)], v);
-      zs[b.l] = v / LU[base + p];
+        if (in_pattern<OP>(pl, b, s)) v = fma(-LUg[(size_t)s * gs + p], zb[l + slot_ldelta(pl, s)], v);
+      zb[l] = v * LUg[(size_t)(ILU_SLOTS - 1) * gs + p];
     }
     __syncthreads();
   }
   double v2[2] = {0.0, 0.0};
-  for (int p = threadIdx.x; p < pl.bs; p += IB) {
-    BlockCell b = block_cell(d, pl, blk, p);
-    double zv = zs[b.l], rv = r[b.c];
-    z[b.c] = zv;
+  for (int q = threadIdx.x; q < gcount * pl.bs; q += GB) {
+    const int bb = q / pl.bs, l = q - bb * pl.bs;
+    const long long c = block_cell(d, pl, b0 + bb, l).c;
+    const double zv = zs[q], rv = r[c];
+    z[c] = zv;
     v2[0] = fma(rv, zv, v2[0]);
     v2[1] = fma(rv, rv, v2[1]);
   }
   double tot[2];
-  if (grid_sum<2, IB>(v2, partials, counter, tot) && threadIdx.x == 0) finalize_dots(st, tot[0], tot[1], init != 0);
+  if (grid_sum<2, GB>(v2, partials, counter, tot) && threadIdx.x == 0) finalize_dots(st, tot[0], tot[1], init != 0);
 }
 
 unsigned int stride_grid(const rkl_ctx *ctx) {
@@ -415,17 +446,42 @@ int bilu0_prepare(rkl_ctx *ctx, const int *block, double dt) {
     IluPlan &pl = ctx->plan;
     pl.bi = bi; pl.bj = bj; pl.bk = bk; pl.bs = bs; pl.nlev = nlev;
     pl.nbi = d.nr / bi; pl.nbj = d.nth / bj; pl.nbk = d.nph / bk;
+    pl.nblocks = pl.nbi * pl.nbj * pl.nbk;
+    // G blocks per CTA: enough rows per wavefront to fill the warps, G * bs <= 8192
+    // cells (64 KB of shared memory for the residual / solution of the group)
+    pl.G = std::max(1, std::min(64, 8192 / bs));
+    pl.ngroups = (pl.nblocks + pl.G - 1) / pl.G;
     pl.lev_start = ctx->plan_buf;
     pl.lev_cell = ctx->plan_buf + nlev + 1;
     pl.pos_of = ctx->plan_buf + nlev + 1 + bs;
+    // the attribute is per function (shared by all contexts): always allow the largest group
+    const int smem = (int)(sizeof(double) * 8192);
+    rc = cuda_check(ctx, cudaFuncSetAttribute(k_bilu_apply<RKL_OP_CONDUCTION>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
+                    "ILU shared memory");
+    if (!rc)
+      rc = cuda_check(ctx, cudaFuncSetAttribute(k_bilu_apply<RKL_OP_VISCOSITY>,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
+                      "ILU shared memory");
+    if (rc) return rc;
   }
-  int rc = ensure_buffer(ctx, &ctx->LU, (size_t)NSL * d.N, "block-ILU0 factors");
-  if (rc) return rc;
-  unsigned int nblk = (unsigned int)(ctx->plan.nbi * ctx->plan.nbj * ctx->plan.nbk);
+  const size_t need = (size_t)ILU_SLOTS * ctx->plan.ngroups * ctx->plan.G * ctx->plan.bs;
+  int rc;
+  if (need > ctx->lu_cap) {
+    if (ctx->LU) {
+      if ((rc = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "ILU resize"))) return rc;
+      cudaFree(ctx->LU);
+      ctx->LU = nullptr;
+      ctx->lu_cap = 0;
+    }
+    if ((rc = cuda_check(ctx, cudaMalloc(&ctx->LU, need * sizeof(double)), "block-ILU0 factors"))) return rc;
+    ctx->lu_cap = need;
+  }
+  const unsigned int ngrp = (unsigned int)ctx->plan.ngroups;
   if (ctx->op == RKL_OP_CONDUCTION)
-    k_bilu_factor<RKL_OP_CONDUCTION><<<nblk, IB, 0, ctx->stream>>>(d, ctx->plan, ctx->coef, ctx->W, dt, ctx->LU);
+    k_bilu_factor<RKL_OP_CONDUCTION><<<ngrp, GB, 0, ctx->stream>>>(d, ctx->plan, ctx->coef, ctx->W, dt, ctx->LU);
   else
-    k_bilu_factor<RKL_OP_VISCOSITY><<<nblk, IB, 0, ctx->stream>>>(d, ctx->plan, ctx->coef, ctx->W, dt, ctx->LU);
+    k_bilu_factor<RKL_OP_VISCOSITY><<<ngrp, GB, 0, ctx->stream>>>(d, ctx->plan, ctx->coef, ctx->W, dt, ctx->LU);
   ctx->launches += 1;
   rc = cuda_check(ctx, cudaGetLastError(), "block-ILU0 factor launch");
   if (rc) return rc;
@@ -467,9 +523,9 @@ static int pcg_run(rkl_ctx *ctx, double *x, const double *u, const double *x0, d
   if (pc == RKL_PC_JACOBI) {
     k_jacobi_init<<<g, RB, 0, ctx->stream>>>(N, ctx->r, ctx->dinv, ctx->p, ctx->partials, ctx->counter, ctx->d_state);
   } else {
-    nblk = (unsigned int)(ctx->plan.nbi * ctx->plan.nbj * ctx->plan.nbk);
-    smem = sizeof(double) * ctx->plan.bs;
-    k_bilu_apply<OP><<<nblk, IB, smem, ctx->stream>>>(d, ctx->plan, ctx->LU, ctx->r, ctx->zbuf, ctx->partials,
+    nblk = (unsigned int)ctx->plan.ngroups;
+    smem = sizeof(double) * ctx->plan.G * ctx->plan.bs;
+    k_bilu_apply<OP><<<nblk, GB, smem, ctx->stream>>>(d, ctx->plan, ctx->LU, ctx->r, ctx->zbuf, ctx->partials,
                                                       ctx->counter, ctx->d_state, 1);
     k_pupdate_z<<<g, RB, 0, ctx->stream>>>(N, ctx->zbuf, ctx->p, ctx->d_state, 1);
   }
@@ -492,7 +548,7 @@ static int pcg_run(rkl_ctx *ctx, double *x, const double *u, const double *x0, d
         k_pupdate_jacobi<<<g, RB, 0, ctx->stream>>>(N, ctx->r, ctx->dinv, ctx->p, ctx->d_state);
       } else {
         k_xr_update<<<g, RB, 0, ctx->stream>>>(N, x, ctx->p, ctx->r, ctx->y, ctx->d_state);
-        k_bilu_apply<OP><<<nblk, IB, smem, ctx->stream>>>(d, ctx->plan, ctx->LU, ctx->r, ctx->zbuf,
+        k_bilu_apply<OP><<<nblk, GB, smem, ctx->stream>>>(d, ctx->plan, ctx->LU, ctx->r, ctx->zbuf,
                                                           ctx->partials, ctx->counter, ctx->d_state, 0);
         k_pupdate_z<<<g, RB, 0, ctx->stream>>>(N, ctx->zbuf, ctx->p, ctx->d_state, 0);
       }
