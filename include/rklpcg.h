@@ -130,6 +130,31 @@ int be_pcg_solve(rkl_ctx *ctx, double *u, int ncomp, double dt, int pc, const in
                  double rtol, int maxit, const double *x0, int *iters_out,
                  double *relres_out);
 
+/* Allocation-free conduction super-step: set_coeffs(RKL_OP_CONDUCTION) followed by
+ * rkl2_superstep, without a context, for callers that cannot call cudaMalloc -- a host
+ * code whose own pool owns all device memory and fixes its footprint at start-up, or a
+ * time loop that cannot afford the device-wide synchronisation that cudaMalloc and
+ * cudaFree may cause.  The paper has no counterpart: this packages the same operator
+ * set-up and super-step with no memory management.
+ * Everything kept between kernels (geometry tables, frozen coefficients, W, 1/W, M0 and
+ * two stage fields, the Gershgorin maximum) lives in one static device array of this
+ * library, about 12.6 MiB, which a GPU holds from its first use until the process exits;
+ * hence nr <= 1024, nth <= 1024 and nr*nth*nph <= 65536 cells (RKL_EINVAL beyond).
+ * T [N], bhat [3N], n [N] and u [N] must be device pointers (RKL_EINVAL otherwise); u is
+ * advanced in place.  kappa0 and coeff_flags are those of set_coeffs; dt, s (0: Eq. 5
+ * with the dt_exp computed here) and flags those of rkl2_superstep.  dt_exp_out and
+ * s_used (host, may be NULL) receive dt_exp and the number of stages.
+ * The first call on a device looks up the device address of the static array with that
+ * device current (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls on a device share the array, which keeps the last call's contents: calls
+ * that overlap on the GPU (several streams or host threads) race and must be serialised
+ * by the caller.  The call returns once dt_exp is known (one small device-to-host read);
+ * the stage kernels then run asynchronously on cuda_stream. */
+int rkl2_superstep_noalloc(const rkl_grid *g, const double *T, const double *bhat,
+                           const double *n, double kappa0, int coeff_flags, double *u,
+                           double dt, int s, int flags, void *cuda_stream, double *dt_exp_out,
+                           int *s_used);
+
 #ifdef __cplusplus
 }
 #endif

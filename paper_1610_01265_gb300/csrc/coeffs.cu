@@ -303,6 +303,17 @@ int launch_setup_conduction(rkl_ctx *ctx, const double *T, const double *bhat, c
   return cuda_check(ctx, cudaGetLastError(), "set_coeffs(conduction) launch");
 }
 
+int launch_setup_conduction_raw(const Dims &d, const Geo &g, cudaStream_t stream, const double *T,
+                                const double *bhat, const double *n, double kappa0, int flags,
+                                double *kappa, double *FS, double *W, double *invW, double *coef,
+                                unsigned long long *lammax, int *flag) {
+  unsigned grid = grid_for(d.N, BLK);
+  k_cell_cond<<<grid, BLK, 0, stream>>>(d, g, T, bhat, n, kappa0, flags, kappa, W, invW, flag);
+  k_faces_cond<<<grid, BLK, 0, stream>>>(d, g, bhat, kappa, FS);
+  k_assemble_cond<<<grid, BLK, 0, stream>>>(d, g, FS, invW, coef, lammax, flag);
+  return cudaGetLastError() == cudaSuccess ? RKL_OK : RKL_ECUDA;
+}
+
 int launch_setup_viscosity(rkl_ctx *ctx, const double *rho, const double *nu) {
   const Dims &d = ctx->d;
   unsigned grid = grid_for(d.N, BLK);

@@ -165,6 +165,20 @@ int launch_rkl2_stage(rkl_ctx *ctx, const double *Ym1, const double *Ym2, const 
                       const double *M0, double *Yout, double mu, double nu, double mutdt,
                       double gtdt);
 
+// context-free launchers (explicit buffers, conduction), used by the allocation-free
+// super-step of noalloc.cu
+int launch_setup_conduction_raw(const Dims &d, const Geo &g, cudaStream_t stream, const double *T,
+                                const double *bhat, const double *n, double kappa0, int flags,
+                                double *kappa, double *FS, double *W, double *invW, double *coef,
+                                unsigned long long *lammax, int *flag);
+int launch_rkl2_first_raw(const Dims &d, cudaStream_t stream, const double *coef,
+                          const double *invW, const double *Y0, double *M0, double *Y1,
+                          double mut1dt);
+int launch_rkl2_stage_raw(const Dims &d, cudaStream_t stream, const double *coef,
+                          const double *invW, const double *Ym1, const double *Ym2,
+                          const double *Y0, const double *M0, double *Yout, double mu, double nu,
+                          double mutdt, double gtdt);
+
 // pcg.cu
 int pcg_solve_component(rkl_ctx *ctx, double *x, const double *u, const double *x0, double dt,
                         int pc, double rtol, int maxit, int *iters, double *relres,

@@ -111,4 +111,20 @@ int launch_rkl2_stage(rkl_ctx *ctx, const double *Ym1, const double *Ym2, const 
   return cuda_check(ctx, cudaGetLastError(), "rkl2 stage launch");
 }
 
+int launch_rkl2_first_raw(const Dims &d, cudaStream_t stream, const double *coef,
+                          const double *invW, const double *Y0, double *M0, double *Y1,
+                          double mut1dt) {
+  k_rkl2_first<RKL_OP_CONDUCTION><<<grid_for(d.N, BLK), BLK, 0, stream>>>(d, coef, invW, Y0, M0, Y1, mut1dt);
+  return cudaGetLastError() == cudaSuccess ? RKL_OK : RKL_ECUDA;
+}
+
+int launch_rkl2_stage_raw(const Dims &d, cudaStream_t stream, const double *coef,
+                          const double *invW, const double *Ym1, const double *Ym2,
+                          const double *Y0, const double *M0, double *Yout, double mu, double nu,
+                          double mutdt, double gtdt) {
+  k_rkl2_stage<RKL_OP_CONDUCTION><<<grid_for(d.N, BLK), BLK, 0, stream>>>(
+      d, coef, invW, Ym1, Ym2, Y0, M0, Yout, mu, nu, 1.0 - mu - nu, mutdt, gtdt);
+  return cudaGetLastError() == cudaSuccess ? RKL_OK : RKL_ECUDA;
+}
+
 }  // namespace rkl

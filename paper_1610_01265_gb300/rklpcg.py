@@ -34,7 +34,7 @@ RKL_FORCE_ODD = 1
 
 EXPORTED = ("rkl_create", "rkl_destroy", "rkl_set_stream", "rkl_strerror", "rkl_last_error",
             "rkl_kernel_launches", "rkl2_stage_count", "set_coeffs", "apply_F", "rkl2_superstep",
-            "be_pcg_solve")
+            "be_pcg_solve", "rkl2_superstep_noalloc")
 
 
 class RklError(RuntimeError):
@@ -83,6 +83,8 @@ def load(path: str | None = None):
     lib.rkl2_superstep.argtypes = [P, P, I, D, D, I, I, ctypes.POINTER(I)]
     lib.be_pcg_solve.argtypes = [P, P, I, D, I, ctypes.POINTER(I), D, I, P, ctypes.POINTER(I),
                                  ctypes.POINTER(D)]
+    lib.rkl2_superstep_noalloc.argtypes = [ctypes.POINTER(_Grid), P, P, P, D, I, P, D, I, I, P,
+                                           ctypes.POINTER(D), ctypes.POINTER(I)]
     _lib = lib
     return lib
 
@@ -96,6 +98,27 @@ def rkl2_stage_count(dt_over_dt_exp: float, flags: int = 0) -> int:
     if s < 0:
         raise RklError(s, "rkl2_stage_count")
     return s
+
+
+def rkl2_superstep_noalloc(r_faces, nth: int, nph: int, T, bhat, n, u, dt: float, kappa0: float = 9e-7,
+                           beta_tcut: bool = False, s: int = 0, force_odd: bool = False, stream=None):
+    """Conduction set-up + one RKL2 super-step with no device allocation (device arrays only);
+    for callers whose memory is owned elsewhere.  Returns (s_used, dt_exp)."""
+    lib = load()
+    rf = np.ascontiguousarray(r_faces, dtype=np.float64)
+    nr = len(rf) - 1
+    N = nr * int(nth) * int(nph)
+    g = _Grid(nr, int(nth), int(nph), rf.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    dte = ctypes.c_double(0.0)
+    used = ctypes.c_int(0)
+    code = lib.rkl2_superstep_noalloc(ctypes.byref(g), _ptr(T, N), _ptr(bhat, 3 * N), _ptr(n, N), float(kappa0),
+                                      RKL_BETA_TCUT if beta_tcut else 0, _ptr(u, N), float(dt), int(s),
+                                      RKL_FORCE_ODD if force_odd else 0,
+                                      stream if stream is not None else _current_stream(),
+                                      ctypes.byref(dte), ctypes.byref(used))
+    if code != RKL_OK:
+        raise RklError(code, "rkl2_superstep_noalloc")
+    return used.value, dte.value
 
 
 def _ptr(a, n: int | None = None):
