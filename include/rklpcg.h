@@ -81,6 +81,29 @@ int rkl_set_stream(rkl_ctx *ctx, void *cuda_stream);
 const char *rkl_strerror(int code);
 const char *rkl_last_error(const rkl_ctx *ctx);
 
+/* Kernel families timed by the optional profiler. */
+enum {
+  RKL_K_SETUP = 0,       /* set_coeffs kernels (one record per call) */
+  RKL_K_APPLY_F = 1,
+  RKL_K_RKL2_FIRST = 2,  /* stage 1: M0 = F(Y0), Y1 */
+  RKL_K_RKL2_STAGE = 3,  /* fused stencil + stage j >= 2 */
+  RKL_K_PCG_INIT = 4,    /* r0, first preconditioner application, p0 */
+  RKL_K_SPMV = 5,        /* y = (W + dt S) p, p.y */
+  RKL_K_PCG_UPDATE = 6,  /* x, r update (+ Jacobi z, r.z, r.r) */
+  RKL_K_PCG_PUPDATE = 7, /* p = z + beta p */
+  RKL_K_BILU_FACTOR = 8,
+  RKL_K_BILU_APPLY = 9,  /* block-ILU0 solve + r.z, r.r */
+  RKL_K_COUNT = 10
+};
+
+/* Per-kernel timing with CUDA events recorded on the context's stream around every
+ * launch (instrumentation; no paper counterpart).  on != 0 clears the counters and starts
+ * recording, 0 stops.  PCG launches queued after convergence, which return at once, are
+ * not counted.  rkl_profile_read synchronises the stream and returns the total time (ms)
+ * and the number of counted launches of one family. */
+int rkl_profile_enable(rkl_ctx *ctx, int on);
+int rkl_profile_read(rkl_ctx *ctx, int kernel, double *total_ms, long long *launches);
+
 /* Number of CUDA kernels this context has launched since rkl_create (instrumentation:
  * every launch of every entry point is counted, including PCG iterations queued after
  * convergence that return at once).  -1 for a NULL context.  No paper counterpart. */

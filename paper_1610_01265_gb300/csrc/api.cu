@@ -227,6 +227,7 @@ int rkl_create(rkl_ctx **out, const rkl_grid *g, int prec, void *stream) {
 int rkl_destroy(rkl_ctx *ctx) {
   if (!ctx) return RKL_OK;
   cudaStreamSynchronize(ctx->stream);
+  prof_release(ctx);
   double *bufs[] = {ctx->geo_buf, ctx->coef, ctx->W, ctx->invW, ctx->scratch, ctx->M0, ctx->Ya, ctx->Yb,
                     ctx->r, ctx->p, ctx->y, ctx->zbuf, ctx->dinv, ctx->partials, ctx->LU, ctx->stage, ctx->stage2};
   for (double *b : bufs)

@@ -9,7 +9,7 @@
 // Vt_f = A_f h_f, D_f = (D_L + D_R)/2, D_x = kappa_x bhat_x bhat_x^T.  Each face adds
 // a small symmetric block to S; the assembly here is a gather: one thread per cell
 // walks every face that touches its row (its own 6 faces and the 24 faces for which
-// it is a transverse neighbour) and keeps the row in registers/local memory.
+// it is a transverse neighbour) and keeps the row in registers.
 //
 // Viscosity: Q_v = 1/2 sum_f Vt_f mu_f g_f^2 (7-point), mu = nu rho, W = rho V.
 #include <cuda_runtime.h>
@@ -23,97 +23,10 @@ namespace {
 
 constexpr int BLK = 256;
 
-struct C3 {
-  int i, j, k;
-};
-
-__device__ __forceinline__ bool same(C3 a, C3 b) { return a.i == b.i && a.j == b.j && a.k == b.k; }
-
-__device__ __forceinline__ int wrapk(const Dims &d, int k) {
-  return k < 0 ? k + d.nph : (k >= d.nph ? k - d.nph : k);
-}
-
-__device__ __forceinline__ long long lin(const Dims &d, C3 x) {
-  return ((long long)x.k * d.nth + x.j) * d.nr + x.i;
-}
-
-// one step along direction a (sign sg) without mirroring; false if it leaves r/theta range
-__device__ __forceinline__ bool step(const Dims &d, C3 x, int a, int sg, C3 &out) {
-  out = x;
-  if (a == 0) {
-    out.i += sg;
-    return out.i >= 0 && out.i < d.nr;
-  }
-  if (a == 1) {
-    out.j += sg;
-    return out.j >= 0 && out.j < d.nth;
-  }
-  out.k = wrapk(d, x.k + sg);
-  return true;
-}
-
-// transverse neighbour used by a centred difference: mirror ghost = the cell itself
-__device__ __forceinline__ C3 mirror_step(const Dims &d, C3 x, int b, int sg) {
-  C3 o;
-  return step(d, x, b, sg, o) ? o : x;
-}
-
-__device__ __forceinline__ bool has_upper_face(const Dims &d, C3 x, int a) {
-  return a == 0 ? x.i < d.nr - 1 : (a == 1 ? x.j < d.nth - 1 : true);
-}
-
-// span of the centred b-difference at x
-__device__ __forceinline__ double cspan(const Geo &g, int b, C3 x) {
-  if (b == 0) return g.dr[x.i];
-  if (b == 1) return 2.0 * g.rc[x.i] * g.dth;
-  return 2.0 * g.rc[x.i] * g.stc[x.j] * g.dph;
-}
-
-__device__ __forceinline__ int transverse(int a, int t) {
-  return a == 0 ? (t ? 2 : 1) : (a == 1 ? (t ? 2 : 0) : (t ? 1 : 0));
-}
-
-__device__ __forceinline__ void row_add(double *row, const Dims &d, C3 c, C3 X, double v,
-                                        int *flag) {
-  int di = X.i - c.i, dj = X.j - c.j, dk = X.k - c.k;
-  if (dk == d.nph - 1) dk = -1;
-  else if (dk == -(d.nph - 1)) dk = 1;
-  if (di < -1 || di > 1 || dj < -1 || dj > 1 || dk < -1 || dk > 1) {
-    atomicOr(flag, 2);  // cannot happen for a face that touches c; reported, not trapped
-    return;
-  }
-  row[(di + 1) + 3 * (dj + 1) + 9 * (dk + 1)] += v;
-}
-
-// contribution of the upper a-face of L (L, R = L + e_a) to row c of S
-__device__ void face_into_row(double *row, const Dims &d, const Geo &g, const double *FS, C3 c,
-                              int a, C3 L, int *flag) {
-  C3 R;
-  step(d, L, a, +1, R);
-  long long l = lin(d, L);
-  double alpha = FS[(3 * a + 0) * d.N + l];
-  double beta[2] = {FS[(3 * a + 1) * d.N + l], FS[(3 * a + 2) * d.N + l]};
-  double sc = same(c, R) ? 1.0 : (same(c, L) ? -1.0 : 0.0);
-  if (sc != 0.0) {
-    row_add(row, d, c, L, -alpha * sc, flag);
-    row_add(row, d, c, R, alpha * sc, flag);
-  }
-  for (int t = 0; t < 2; t++) {
-    int b = transverse(a, t);
-    double gl = 0.5 / cspan(g, b, L), gr = 0.5 / cspan(g, b, R);
-    C3 X[4] = {mirror_step(d, L, b, +1), mirror_step(d, L, b, -1), mirror_step(d, R, b, +1),
-               mirror_step(d, R, b, -1)};
-    double w[4] = {gl, -gl, gr, -gr};
-    for (int q = 0; q < 4; q++) {
-      // d^2 Q / du_c du_X from the g * ghat_b term: beta (sigma_c w_X + w_c sigma_X)
-      if (sc != 0.0) row_add(row, d, c, X[q], beta[t] * sc * w[q], flag);
-      if (same(X[q], c)) {
-        row_add(row, d, c, L, -beta[t] * w[q], flag);
-        row_add(row, d, c, R, beta[t] * w[q], flag);
-      }
-    }
-  }
-}
+// slot of offset (di, dj, dk) in a 27-entry row; t-th transverse direction of a; unit vector
+__host__ __device__ constexpr int r27(int di, int dj, int dk) { return (di + 1) + 3 * (dj + 1) + 9 * (dk + 1); }
+__host__ __device__ constexpr int tdir(int a, int t) { return a == 0 ? (t ? 2 : 1) : (a == 1 ? (t ? 2 : 0) : (t ? 1 : 0)); }
+__host__ __device__ constexpr int ex_(int a, int x) { return a == x ? 1 : 0; }
 
 __global__ void k_cell_cond(Dims d, Geo g, const double *__restrict__ T,
                             const double *__restrict__ bhat, const double *__restrict__ n,
@@ -172,7 +85,7 @@ __global__ void k_faces_cond(Dims d, Geo g, const double *__restrict__ bhat,
       double Vt = A * h;
       double kR = kappa[R];
       double bR[3] = {bhat[R], bhat[N + R], bhat[2 * N + R]};
-      int t0 = transverse(a, 0), t1 = transverse(a, 1);
+      int t0 = tdir(a, 0), t1 = tdir(a, 1);
       double Daa = 0.5 * (kL * bL[a] * bL[a] + kR * bR[a] * bR[a]);
       double Da0 = 0.5 * (kL * bL[a] * bL[t0] + kR * bR[a] * bR[t0]);
       double Da1 = 0.5 * (kL * bL[a] * bL[t1] + kR * bR[a] * bR[t1]);
@@ -186,38 +99,155 @@ __global__ void k_faces_cond(Dims d, Geo g, const double *__restrict__ bhat,
   }
 }
 
-__global__ void k_assemble_cond(Dims d, Geo g, const double *__restrict__ FS,
-                                const double *__restrict__ invW, double *__restrict__ coef,
-                                unsigned long long *lammax, int *flag) {
+// ---- row assembly: every slot index known at compile time ----
+//
+// A face touching the row of cell c is one of 30 cases fixed by its direction A, the
+// position of its L cell relative to c and the role of c (L, R, or a transverse
+// neighbour entering through ghat_b).  Enumerating the cases with templates makes every
+// target slot a compile-time constant; the only runtime choices are whether a face
+// exists and whether a transverse neighbour is a mirror ghost (then the entry goes to
+// L or R instead), so the 27-entry row stays in registers.
+
+
+struct RowCell {
+  int i, j;
+  long long c;
+  bool up[3], dn[3];         // does c + e_a / c - e_a exist (always true along phi)
+  long long dup[3], ddn[3];  // index deltas of c + e_a / c - e_a (phi wrapped)
+};
+
+template <int DI, int DJ, int DK>
+__device__ __forceinline__ bool has(const RowCell &C) {
+  return (DI > 0 ? C.up[0] : (DI < 0 ? C.dn[0] : true)) && (DJ > 0 ? C.up[1] : (DJ < 0 ? C.dn[1] : true));
+}
+
+template <int DI, int DJ, int DK>
+__device__ __forceinline__ long long idx(const RowCell &C) {
+  return C.c + (DI > 0 ? C.dup[0] : (DI < 0 ? C.ddn[0] : 0)) + (DJ > 0 ? C.dup[1] : (DJ < 0 ? C.ddn[1] : 0)) +
+         (DK > 0 ? C.dup[2] : (DK < 0 ? C.ddn[2] : 0));
+}
+
+template <int B, int DI, int DJ>
+__device__ __forceinline__ double gam(const Geo &g, const RowCell &C) {  // 0.5 / span of G_B at c + (DI,DJ,.)
+  const int i = C.i + DI, j = C.j + DJ;
+  if (B == 0) return 0.5 / g.dr[i];
+  if (B == 1) return 0.5 / (2.0 * g.rc[i] * g.dth);
+  return 0.5 / (2.0 * g.rc[i] * g.stc[j] * g.dph);
+}
+
+template <int I1, int I0>
+__device__ __forceinline__ void add_sel(double (&row)[27], bool first, double v) {
+  if (first) row[I1] += v;
+  else row[I0] += v;
+}
+
+// own face of c (c = L when SC = -1, c = R when SC = +1); L at offset (LI, LJ, LK)
+template <int A, int LI, int LJ, int LK, int SC>
+__device__ __forceinline__ void own_face(double (&row)[27], const RowCell &C, const Geo &g,
+                                         const double *__restrict__ FS, long long N) {
+  constexpr int RI = LI + ex_(A, 0), RJ = LJ + ex_(A, 1), RK = LK + ex_(A, 2);
+  if (!has<LI, LJ, LK>(C) || !has<RI, RJ, RK>(C)) return;
+  const long long l = idx<LI, LJ, LK>(C);
+  const double al = FS[(3 * A + 0) * N + l];
+  row[r27(LI, LJ, LK)] += -al * SC;
+  row[r27(RI, RJ, RK)] += al * SC;
+#pragma unroll
+  for (int t = 0; t < 2; t++) {
+    // (t is unrolled; tdir is constexpr-folded)
+    const double be = FS[(3 * A + 1 + t) * N + l];
+    if (t == 0) {
+      constexpr int B = tdir(A, 0), EI = ex_(B, 0), EJ = ex_(B, 1), EK = ex_(B, 2);
+      const bool exp_ = has<EI, EJ, EK>(C), exm = has<-EI, -EJ, -EK>(C);
+      const double gl = gam<B, LI, LJ>(g, C), gr = gam<B, RI, RJ>(g, C);
+      const double v = be * SC;
+      add_sel<r27(LI + EI, LJ + EJ, LK + EK), r27(LI, LJ, LK)>(row, exp_, v * gl);
+      add_sel<r27(LI - EI, LJ - EJ, LK - EK), r27(LI, LJ, LK)>(row, exm, -v * gl);
+      add_sel<r27(RI + EI, RJ + EJ, RK + EK), r27(RI, RJ, RK)>(row, exp_, v * gr);
+      add_sel<r27(RI - EI, RJ - EJ, RK - EK), r27(RI, RJ, RK)>(row, exm, -v * gr);
+      const double wp = SC < 0 ? gl : gr, wm = SC < 0 ? -gl : -gr;  // ghosts of c itself
+      if (!exp_) { row[r27(LI, LJ, LK)] -= be * wp; row[r27(RI, RJ, RK)] += be * wp; }
+      if (!exm) { row[r27(LI, LJ, LK)] -= be * wm; row[r27(RI, RJ, RK)] += be * wm; }
+    } else {
+      constexpr int B = tdir(A, 1), EI = ex_(B, 0), EJ = ex_(B, 1), EK = ex_(B, 2);
+      const bool exp_ = has<EI, EJ, EK>(C), exm = has<-EI, -EJ, -EK>(C);
+      const double gl = gam<B, LI, LJ>(g, C), gr = gam<B, RI, RJ>(g, C);
+      const double v = be * SC;
+      add_sel<r27(LI + EI, LJ + EJ, LK + EK), r27(LI, LJ, LK)>(row, exp_, v * gl);
+      add_sel<r27(LI - EI, LJ - EJ, LK - EK), r27(LI, LJ, LK)>(row, exm, -v * gl);
+      add_sel<r27(RI + EI, RJ + EJ, RK + EK), r27(RI, RJ, RK)>(row, exp_, v * gr);
+      add_sel<r27(RI - EI, RJ - EJ, RK - EK), r27(RI, RJ, RK)>(row, exm, -v * gr);
+      const double wp = SC < 0 ? gl : gr, wm = SC < 0 ? -gl : -gr;
+      if (!exp_) { row[r27(LI, LJ, LK)] -= be * wp; row[r27(RI, RJ, RK)] += be * wp; }
+      if (!exm) { row[r27(LI, LJ, LK)] -= be * wm; row[r27(RI, RJ, RK)] += be * wm; }
+    }
+  }
+}
+
+// A-face of the transverse neighbour x = c + SG e_T(A,TT): the face U_A(x) (LOW = 0) or
+// U_A(x - e_A) (LOW = 1); c enters it as the ghat_B neighbour of x (B = tdir(A, TT)).
+template <int A, int TT, int SG, int LOW>
+__device__ __forceinline__ void trans_face(double (&row)[27], const RowCell &C, const Geo &g,
+                                           const double *__restrict__ FS, long long N) {
+  constexpr int B = tdir(A, TT);
+  constexpr int XI = SG * ex_(B, 0), XJ = SG * ex_(B, 1), XK = SG * ex_(B, 2);
+  constexpr int LI = XI - LOW * ex_(A, 0), LJ = XJ - LOW * ex_(A, 1), LK = XK - LOW * ex_(A, 2);
+  constexpr int RI = LI + ex_(A, 0), RJ = LJ + ex_(A, 1), RK = LK + ex_(A, 2);
+  if (!has<LI, LJ, LK>(C) || !has<RI, RJ, RK>(C)) return;
+  const long long l = idx<LI, LJ, LK>(C);
+  const double be = FS[(3 * A + 1 + TT) * N + l];
+  // c = x - SG e_B, x = L (LOW = 0) or R (LOW = 1): weight of c in ghat_B is -SG gamma_B(x)
+  const double w = LOW ? -SG * gam<B, RI, RJ>(g, C) : -SG * gam<B, LI, LJ>(g, C);
+  row[r27(LI, LJ, LK)] -= be * w;
+  row[r27(RI, RJ, RK)] += be * w;
+}
+
+template <int A>
+__device__ __forceinline__ void faces_of_direction(double (&row)[27], const RowCell &C, const Geo &g,
+                                                   const double *__restrict__ FS, long long N) {
+  own_face<A, 0, 0, 0, -1>(row, C, g, FS, N);
+  own_face<A, -ex_(A, 0), -ex_(A, 1), -ex_(A, 2), +1>(row, C, g, FS, N);
+  trans_face<A, 0, +1, 0>(row, C, g, FS, N);
+  trans_face<A, 0, +1, 1>(row, C, g, FS, N);
+  trans_face<A, 0, -1, 0>(row, C, g, FS, N);
+  trans_face<A, 0, -1, 1>(row, C, g, FS, N);
+  trans_face<A, 1, +1, 0>(row, C, g, FS, N);
+  trans_face<A, 1, +1, 1>(row, C, g, FS, N);
+  trans_face<A, 1, -1, 0>(row, C, g, FS, N);
+  trans_face<A, 1, -1, 1>(row, C, g, FS, N);
+}
+
+__global__ void __launch_bounds__(BLK) k_assemble_cond_fast(Dims d, Geo g, const double *__restrict__ FS,
+                                                            const double *__restrict__ invW,
+                                                            double *__restrict__ coef,
+                                                            unsigned long long *lammax, int *flag) {
   long long cl = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (cl >= d.N) return;
-  C3 c;
-  cell_coords(d, cl, c.i, c.j, c.k);
+  RowCell C;
+  int k;
+  cell_coords(d, cl, C.i, C.j, k);
+  C.c = cl;
+  C.up[0] = C.i < d.nr - 1;
+  C.dn[0] = C.i > 0;
+  C.up[1] = C.j < d.nth - 1;
+  C.dn[1] = C.j > 0;
+  C.up[2] = C.dn[2] = true;
+  C.dup[0] = 1;
+  C.ddn[0] = -1;
+  C.dup[1] = d.nr;
+  C.ddn[1] = -(long long)d.nr;
+  C.dup[2] = (k < d.nph - 1) ? d.nrt : -(long long)(d.nph - 1) * d.nrt;
+  C.ddn[2] = (k > 0) ? -d.nrt : (long long)(d.nph - 1) * d.nrt;
   double row[27];
 #pragma unroll
   for (int q = 0; q < 27; q++) row[q] = 0.0;
-  for (int a = 0; a < 3; a++) {
-    C3 x;
-    // own faces: upper (c = L) and lower (c = R)
-    if (has_upper_face(d, c, a)) face_into_row(row, d, g, FS, c, a, c, flag);
-    if (step(d, c, a, -1, x)) face_into_row(row, d, g, FS, c, a, x, flag);
-    // a-faces of the transverse neighbours c +- e_b: c enters them through ghat_b
-    for (int t = 0; t < 2; t++) {
-      int b = transverse(a, t);
-      for (int sg = -1; sg <= 1; sg += 2) {
-        C3 nb, nbm;
-        if (!step(d, c, b, sg, nb)) continue;
-        if (has_upper_face(d, nb, a)) face_into_row(row, d, g, FS, c, a, nb, flag);
-        if (step(d, nb, a, -1, nbm)) face_into_row(row, d, g, FS, c, a, nbm, flag);
-      }
-    }
-  }
+  faces_of_direction<0>(row, C, g, FS, d.N);
+  faces_of_direction<1>(row, C, g, FS, d.N);
+  faces_of_direction<2>(row, C, g, FS, d.N);
   double sum = 0.0;
 #pragma unroll
   for (int q = 0; q < 27; q++) sum += fabs(row[q]);
 #pragma unroll
-  for (int m = 0; m < 9; m++)
-    coef[m * d.N + cl] = row[(fwd_di(m) + 1) + 3 * (fwd_dj(m) + 1) + 9 * (fwd_dk(m) + 1)];
+  for (int m = 0; m < 9; m++) coef[m * d.N + cl] = row[r27(fwd_di(m), fwd_dj(m), fwd_dk(m))];
   coef[9 * d.N + cl] = row[13];
   double rs = sum * invW[cl];
   if (!isfinite(rs)) atomicOr(flag, 1);
@@ -290,6 +320,7 @@ __global__ void k_assemble_visc(Dims d, Geo g, const double *__restrict__ mu,
 
 int launch_setup_conduction(rkl_ctx *ctx, const double *T, const double *bhat, const double *n,
                             double kappa0, int flags) {
+  ProfScope prof(ctx, RKL_K_SETUP);
   const Dims &d = ctx->d;
   unsigned grid = grid_for(d.N, BLK);
   double *kappa = ctx->scratch;
@@ -297,8 +328,8 @@ int launch_setup_conduction(rkl_ctx *ctx, const double *T, const double *bhat, c
   k_cell_cond<<<grid, BLK, 0, ctx->stream>>>(d, ctx->geo, T, bhat, n, kappa0, flags, kappa, ctx->W,
                                             ctx->invW, ctx->d_flag);
   k_faces_cond<<<grid, BLK, 0, ctx->stream>>>(d, ctx->geo, bhat, kappa, FS);
-  k_assemble_cond<<<grid, BLK, 0, ctx->stream>>>(d, ctx->geo, FS, ctx->invW, ctx->coef,
-                                                ctx->d_lammax, ctx->d_flag);
+  k_assemble_cond_fast<<<grid, BLK, 0, ctx->stream>>>(d, ctx->geo, FS, ctx->invW, ctx->coef,
+                                                     ctx->d_lammax, ctx->d_flag);
   ctx->launches += 3;
   return cuda_check(ctx, cudaGetLastError(), "set_coeffs(conduction) launch");
 }
@@ -310,11 +341,12 @@ int launch_setup_conduction_raw(const Dims &d, const Geo &g, cudaStream_t stream
   unsigned grid = grid_for(d.N, BLK);
   k_cell_cond<<<grid, BLK, 0, stream>>>(d, g, T, bhat, n, kappa0, flags, kappa, W, invW, flag);
   k_faces_cond<<<grid, BLK, 0, stream>>>(d, g, bhat, kappa, FS);
-  k_assemble_cond<<<grid, BLK, 0, stream>>>(d, g, FS, invW, coef, lammax, flag);
+  k_assemble_cond_fast<<<grid, BLK, 0, stream>>>(d, g, FS, invW, coef, lammax, flag);
   return cudaGetLastError() == cudaSuccess ? RKL_OK : RKL_ECUDA;
 }
 
 int launch_setup_viscosity(rkl_ctx *ctx, const double *rho, const double *nu) {
+  ProfScope prof(ctx, RKL_K_SETUP);
   const Dims &d = ctx->d;
   unsigned grid = grid_for(d.N, BLK);
   double *mu = ctx->scratch;

@@ -90,6 +90,11 @@ enum { ILU_SLOTS = 20 };  // 0 U_ii, 1..9 L (lower), 10..18 U (upper), 19 1/U_ii
 
 }  // namespace rkl
 
+struct ProfRec {
+  int kind, tag;
+  cudaEvent_t a, b;
+};
+
 struct rkl_ctx {
   rkl::Dims d;
   int device;
@@ -135,6 +140,13 @@ struct rkl_ctx {
   // number of kernels this context has launched (all entry points)
   long long launches = 0;
 
+  // optional per-kernel event timing (profile.cu)
+  int prof_on = 0;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<ProfRec> prof_pending;
+  double prof_ms[RKL_K_COUNT] = {};
+  long long prof_n[RKL_K_COUNT] = {};
+
   // host-pointer staging
   double *stage = nullptr;
   size_t stage_cap = 0;  // doubles
@@ -143,6 +155,18 @@ struct rkl_ctx {
 };
 
 namespace rkl {
+
+// Brackets one launch (or a fixed group of launches) with events when profiling is on;
+// tag = iteration index inside a PCG chunk, or -1.
+struct ProfScope {
+  rkl_ctx *ctx;
+  int kind, tag;
+  cudaEvent_t a;
+  ProfScope(rkl_ctx *c, int k, int t = -1);
+  ~ProfScope();
+};
+void prof_settle(rkl_ctx *ctx, int n_real, bool still_running, bool chunk);
+void prof_release(rkl_ctx *ctx);
 
 int set_error(rkl_ctx *ctx, int code, const std::string &msg);
 int cuda_check(rkl_ctx *ctx, cudaError_t e, const char *what);

@@ -331,66 +331,158 @@ __global__ void __launch_bounds__(GB) k_bilu_factor(Dims d, IluPlan pl,
 }
 
 // z = (LU)^{-1} r on G blocks: residual staged in shared memory, forward (unit L) and
-// backward (U, times 1/U_ii) sweeps wavefront by wavefront, then r.z and r.r
+// backward (U, times 1/U_ii) sweeps wavefront by wavefront, then r.z and r.r.
+// G is chosen so that a wavefront of the group has at most AB rows: each thread owns at
+// most one row per wavefront and loads the factors of its next row before the barrier,
+// so their latency overlaps the current wavefront.  Per-position data (local index,
+// pattern mask, offset in the grid) is tabulated once per CTA in shared memory.
+constexpr int AB = 384;
+constexpr int ILU_TAB_BYTES = 8192 * 8 + 4096 * 4 * 2 + 64 * 8;  // zs + tab + goff + base
+
 template <int OP>
-__global__ void __launch_bounds__(GB) k_bilu_apply(Dims d, IluPlan pl,
+__global__ void __launch_bounds__(AB) k_bilu_apply(Dims d, IluPlan pl,
                                                    const double *__restrict__ LU,
                                                    const double *__restrict__ r,
                                                    double *__restrict__ z, double *partials,
                                                    unsigned int *counter, PcgState *st,
                                                    int init) {
   if (!init && st->status != PCG_RUNNING) return;
-  extern __shared__ double zs[];  // [G][bs]
+  extern __shared__ double smem[];
+  const int bs = pl.bs;
+  double *zs = smem;                                        // [G][bs] by local index
+  long long *base = (long long *)(zs + (size_t)pl.G * bs);  // [G] grid index of block origin
+  int *tab = (int *)(base + pl.G);                          // [bs] level order: l | mask << 12
+  int *goff = tab + bs;                                     // [bs] by local index
   const int grp = blockIdx.x, b0 = grp * pl.G;
   const int gcount = min(pl.G, pl.nblocks - b0);
-  const size_t gs = (size_t)pl.G * pl.bs;
+  const size_t gs = (size_t)pl.G * bs;
   const double *LUg = LU + (size_t)grp * ILU_SLOTS * gs;
-  for (int q = threadIdx.x; q < gcount * pl.bs; q += GB) {
-    const int bb = q / pl.bs, l = q - bb * pl.bs;
-    zs[q] = r[block_cell(d, pl, b0 + bb, l).c];
+  const int tid = threadIdx.x;
+
+  for (int pp = tid; pp < bs; pp += AB) {
+    const int l = pl.lev_cell[pp];
+    BlockCell b;
+    b.li = l % pl.bi;
+    b.lj = (l / pl.bi) % pl.bj;
+    b.lk = l / (pl.bi * pl.bj);
+    int mask = 0;
+#pragma unroll
+    for (int s = 1; s < NSL; s++)
+      if (in_pattern<OP>(pl, b, s)) mask |= 1 << (s - 1);
+    tab[pp] = l | (mask << 12);
+    goff[l] = (int)(b.li + (long long)d.nr * b.lj + d.nrt * b.lk);
+  }
+  for (int bb = tid; bb < gcount; bb += AB) {
+    const int blk = b0 + bb;
+    const int bI = blk % pl.nbi, bJ = (blk / pl.nbi) % pl.nbj, bK = blk / (pl.nbi * pl.nbj);
+    base[bb] = ((long long)(bK * pl.bk) * d.nth + bJ * pl.bj) * d.nr + bI * pl.bi;
+  }
+  __syncthreads();
+  for (int q = tid; q < gcount * bs; q += AB) {
+    const int bb = q / bs;
+    zs[q] = r[base[bb] + goff[q - bb * bs]];
+  }
+  int dl[NSL];  // local-index offset of every slot
+#pragma unroll
+  for (int s = 0; s < NSL; s++) dl[s] = slot_ldelta(pl, s);
+
+  // ---- forward sweep: z* = r - L z* ----
+  double pre[9];
+  {
+    const int nl = pl.lev_start[1] - pl.lev_start[0];
+    if (tid < gcount * nl) {
+#pragma unroll
+      for (int s = 1; s < 10; s++) pre[s - 1] = LUg[(size_t)s * gs + tid];
+    }
   }
   __syncthreads();
   for (int lev = 0; lev < pl.nlev; lev++) {
     const int ls = pl.lev_start[lev], nl = pl.lev_start[lev + 1] - ls;
-    for (int q = threadIdx.x; q < gcount * nl; q += GB) {
-      const int bb = q / nl, l = pl.lev_cell[ls + (q - bb * nl)];
-      const size_t p = (size_t)pl.G * ls + q;
-      BlockCell b = block_cell(d, pl, b0 + bb, l);
-      double *zb = zs + bb * pl.bs;
-      double v = zb[l];
+    double cur[9];
 #pragma unroll
-      for (int s = 1; s < 10; s++)
-        if (in_pattern<OP>(pl, b, s)) v = fma(-LUg[(size_t)s * gs + p], zb[l + slot_ldelta(pl, s)], v);
+    for (int s = 0; s < 9; s++) cur[s] = pre[s];
+    if (lev + 1 < pl.nlev) {
+      const int ls2 = pl.lev_start[lev + 1], nl2 = pl.lev_start[lev + 2] - ls2;
+      if (tid < gcount * nl2) {
+        const size_t p2 = (size_t)pl.G * ls2 + tid;
+#pragma unroll
+        for (int s = 1; s < 10; s++) pre[s - 1] = LUg[(size_t)s * gs + p2];
+      }
+    }
+    for (int q = tid; q < gcount * nl; q += AB) {
+      const int bb = q / nl;
+      const int t = tab[ls + (q - bb * nl)], l = t & 0xfff, mask = t >> 12;
+      double *zb = zs + bb * bs;
+      double v = zb[l];
+      if (q == tid) {
+#pragma unroll
+        for (int s = 1; s < 10; s++)
+          if (mask & (1 << (s - 1))) v = fma(-cur[s - 1], zb[l + dl[s]], v);
+      } else {
+        const size_t p = (size_t)pl.G * ls + q;
+#pragma unroll
+        for (int s = 1; s < 10; s++)
+          if (mask & (1 << (s - 1))) v = fma(-LUg[(size_t)s * gs + p], zb[l + dl[s]], v);
+      }
       zb[l] = v;
     }
     __syncthreads();
   }
+
+  // ---- backward sweep: z = (z* - U z) / U_ii ----
+  double preb[10];
+  {
+    const int lsl = pl.lev_start[pl.nlev - 1], nl = pl.lev_start[pl.nlev] - lsl;
+    if (tid < gcount * nl) {
+      const size_t p = (size_t)pl.G * lsl + tid;
+#pragma unroll
+      for (int s = 10; s < ILU_SLOTS; s++) preb[s - 10] = LUg[(size_t)s * gs + p];
+    }
+  }
   for (int lev = pl.nlev - 1; lev >= 0; lev--) {
     const int ls = pl.lev_start[lev], nl = pl.lev_start[lev + 1] - ls;
-    for (int q = threadIdx.x; q < gcount * nl; q += GB) {
-      const int bb = q / nl, l = pl.lev_cell[ls + (q - bb * nl)];
-      const size_t p = (size_t)pl.G * ls + q;
-      BlockCell b = block_cell(d, pl, b0 + bb, l);
-      double *zb = zs + bb * pl.bs;
-      double v = zb[l];
+    double cur[10];
 #pragma unroll
-      for (int s = 10; s < NSL; s++)
-        if (in_pattern<OP>(pl, b, s)) v = fma(-LUg[(size_t)s * gs + p], zb[l + slot_ldelta(pl, s)], v);
-      zb[l] = v * LUg[(size_t)(ILU_SLOTS - 1) * gs + p];
+    for (int s = 0; s < 10; s++) cur[s] = preb[s];
+    if (lev > 0) {
+      const int ls2 = pl.lev_start[lev - 1], nl2 = ls - ls2;
+      if (tid < gcount * nl2) {
+        const size_t p2 = (size_t)pl.G * ls2 + tid;
+#pragma unroll
+        for (int s = 10; s < ILU_SLOTS; s++) preb[s - 10] = LUg[(size_t)s * gs + p2];
+      }
+    }
+    for (int q = tid; q < gcount * nl; q += AB) {
+      const int bb = q / nl;
+      const int t = tab[ls + (q - bb * nl)], l = t & 0xfff, mask = t >> 12;
+      double *zb = zs + bb * bs;
+      double v = zb[l];
+      if (q == tid) {
+#pragma unroll
+        for (int s = 10; s < NSL; s++)
+          if (mask & (1 << (s - 1))) v = fma(-cur[s - 10], zb[l + dl[s]], v);
+        zb[l] = v * cur[9];
+      } else {
+        const size_t p = (size_t)pl.G * ls + q;
+#pragma unroll
+        for (int s = 10; s < NSL; s++)
+          if (mask & (1 << (s - 1))) v = fma(-LUg[(size_t)s * gs + p], zb[l + dl[s]], v);
+        zb[l] = v * LUg[(size_t)(ILU_SLOTS - 1) * gs + p];
+      }
     }
     __syncthreads();
   }
   double v2[2] = {0.0, 0.0};
-  for (int q = threadIdx.x; q < gcount * pl.bs; q += GB) {
-    const int bb = q / pl.bs, l = q - bb * pl.bs;
-    const long long c = block_cell(d, pl, b0 + bb, l).c;
+  for (int q = tid; q < gcount * bs; q += AB) {
+    const int bb = q / bs;
+    const long long c = base[bb] + goff[q - bb * bs];
     const double zv = zs[q], rv = r[c];
     z[c] = zv;
     v2[0] = fma(rv, zv, v2[0]);
     v2[1] = fma(rv, rv, v2[1]);
   }
   double tot[2];
-  if (grid_sum<2, GB>(v2, partials, counter, tot) && threadIdx.x == 0) finalize_dots(st, tot[0], tot[1], init != 0);
+  if (grid_sum<2, AB>(v2, partials, counter, tot) && threadIdx.x == 0) finalize_dots(st, tot[0], tot[1], init != 0);
 }
 
 unsigned int stride_grid(const rkl_ctx *ctx) {
@@ -447,15 +539,17 @@ int bilu0_prepare(rkl_ctx *ctx, const int *block, double dt) {
     pl.bi = bi; pl.bj = bj; pl.bk = bk; pl.bs = bs; pl.nlev = nlev;
     pl.nbi = d.nr / bi; pl.nbj = d.nth / bj; pl.nbk = d.nph / bk;
     pl.nblocks = pl.nbi * pl.nbj * pl.nbk;
-    // G blocks per CTA: enough rows per wavefront to fill the warps, G * bs <= 8192
-    // cells (64 KB of shared memory for the residual / solution of the group)
-    pl.G = std::max(1, std::min(64, 8192 / bs));
+    // G blocks per CTA: enough rows per wavefront to fill the warps but at most AB rows
+    // per wavefront of the group, and G * bs <= 8192 cells of shared memory
+    int maxlev = 0;
+    for (int l = 0; l < nlev; l++) maxlev = std::max(maxlev, start[l + 1] - start[l]);
+    pl.G = std::max(1, std::min({64, 8192 / bs, AB / maxlev}));
     pl.ngroups = (pl.nblocks + pl.G - 1) / pl.G;
     pl.lev_start = ctx->plan_buf;
     pl.lev_cell = ctx->plan_buf + nlev + 1;
     pl.pos_of = ctx->plan_buf + nlev + 1 + bs;
     // the attribute is per function (shared by all contexts): always allow the largest group
-    const int smem = (int)(sizeof(double) * 8192);
+    const int smem = ILU_TAB_BYTES;
     rc = cuda_check(ctx, cudaFuncSetAttribute(k_bilu_apply<RKL_OP_CONDUCTION>,
                                               cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
                     "ILU shared memory");
@@ -478,6 +572,7 @@ int bilu0_prepare(rkl_ctx *ctx, const int *block, double dt) {
     ctx->lu_cap = need;
   }
   const unsigned int ngrp = (unsigned int)ctx->plan.ngroups;
+  ProfScope prof(ctx, RKL_K_BILU_FACTOR);
   if (ctx->op == RKL_OP_CONDUCTION)
     k_bilu_factor<RKL_OP_CONDUCTION><<<ngrp, GB, 0, ctx->stream>>>(d, ctx->plan, ctx->coef, ctx->W, dt, ctx->LU);
   else
@@ -511,6 +606,10 @@ static int pcg_run(rkl_ctx *ctx, double *x, const double *u, const double *x0, d
     return rc;
   unsigned int g = stride_grid(ctx);
   const double *xs = x0 ? x0 : u;
+  unsigned int nblk = 0;
+  size_t smem = 0;
+  {
+  ProfScope prof(ctx, RKL_K_PCG_INIT);
   k_r0<OP><<<g, RB, 0, ctx->stream>>>(d, ctx->coef, ctx->W, dt, u, xs, ctx->r,
                                       pc == RKL_PC_JACOBI ? ctx->dinv : nullptr, ctx->partials,
                                       ctx->counter, ctx->d_state);
@@ -518,38 +617,55 @@ static int pcg_run(rkl_ctx *ctx, double *x, const double *u, const double *x0, d
     if ((rc = cuda_check(ctx, cudaMemcpyAsync(x, x0, sizeof(double) * N, cudaMemcpyDeviceToDevice, ctx->stream), "x0 copy")))
       return rc;
   }
-  unsigned int nblk = 0;
-  size_t smem = 0;
   if (pc == RKL_PC_JACOBI) {
     k_jacobi_init<<<g, RB, 0, ctx->stream>>>(N, ctx->r, ctx->dinv, ctx->p, ctx->partials, ctx->counter, ctx->d_state);
   } else {
     nblk = (unsigned int)ctx->plan.ngroups;
-    smem = sizeof(double) * ctx->plan.G * ctx->plan.bs;
-    k_bilu_apply<OP><<<nblk, GB, smem, ctx->stream>>>(d, ctx->plan, ctx->LU, ctx->r, ctx->zbuf, ctx->partials,
+    smem = sizeof(double) * ctx->plan.G * ctx->plan.bs + sizeof(long long) * ctx->plan.G +
+           2 * sizeof(int) * ctx->plan.bs;
+    k_bilu_apply<OP><<<nblk, AB, smem, ctx->stream>>>(d, ctx->plan, ctx->LU, ctx->r, ctx->zbuf, ctx->partials,
                                                       ctx->counter, ctx->d_state, 1);
     k_pupdate_z<<<g, RB, 0, ctx->stream>>>(N, ctx->zbuf, ctx->p, ctx->d_state, 1);
+  }
   }
   ctx->launches += 2;
   if ((rc = cuda_check(ctx, cudaGetLastError(), "PCG init launch"))) return rc;
   const int chunk = 8;
+  int it_prev = 0;
   for (;;) {
     if ((rc = cuda_check(ctx, cudaMemcpyAsync(ctx->h_state, ctx->d_state, sizeof(PcgState),
                                               cudaMemcpyDeviceToHost, ctx->stream), "PCG state read")))
       return rc;
     if ((rc = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "PCG iteration"))) return rc;
     const PcgState &h = *ctx->h_state;
+    if (ctx->prof_on) prof_settle(ctx, h.iters - it_prev, h.status == PCG_RUNNING, true);
+    it_prev = h.iters;
     if (h.status != PCG_RUNNING || h.iters >= maxit) break;
     for (int q = 0; q < chunk; q++) {
-      k_spmv<OP><<<g, RB, 0, ctx->stream>>>(d, ctx->coef, ctx->W, dt, ctx->p, ctx->y, ctx->partials,
-                                            ctx->counter, ctx->d_state);
+      {
+        ProfScope prof(ctx, RKL_K_SPMV, q);
+        k_spmv<OP><<<g, RB, 0, ctx->stream>>>(d, ctx->coef, ctx->W, dt, ctx->p, ctx->y, ctx->partials,
+                                              ctx->counter, ctx->d_state);
+      }
       if (pc == RKL_PC_JACOBI) {
-        k_update_jacobi<<<g, RB, 0, ctx->stream>>>(N, x, ctx->p, ctx->r, ctx->y, ctx->dinv, ctx->partials,
-                                                   ctx->counter, ctx->d_state);
+        {
+          ProfScope prof(ctx, RKL_K_PCG_UPDATE, q);
+          k_update_jacobi<<<g, RB, 0, ctx->stream>>>(N, x, ctx->p, ctx->r, ctx->y, ctx->dinv, ctx->partials,
+                                                     ctx->counter, ctx->d_state);
+        }
+        ProfScope prof(ctx, RKL_K_PCG_PUPDATE, q);
         k_pupdate_jacobi<<<g, RB, 0, ctx->stream>>>(N, ctx->r, ctx->dinv, ctx->p, ctx->d_state);
       } else {
-        k_xr_update<<<g, RB, 0, ctx->stream>>>(N, x, ctx->p, ctx->r, ctx->y, ctx->d_state);
-        k_bilu_apply<OP><<<nblk, GB, smem, ctx->stream>>>(d, ctx->plan, ctx->LU, ctx->r, ctx->zbuf,
-                                                          ctx->partials, ctx->counter, ctx->d_state, 0);
+        {
+          ProfScope prof(ctx, RKL_K_PCG_UPDATE, q);
+          k_xr_update<<<g, RB, 0, ctx->stream>>>(N, x, ctx->p, ctx->r, ctx->y, ctx->d_state);
+        }
+        {
+          ProfScope prof(ctx, RKL_K_BILU_APPLY, q);
+          k_bilu_apply<OP><<<nblk, AB, smem, ctx->stream>>>(d, ctx->plan, ctx->LU, ctx->r, ctx->zbuf,
+                                                            ctx->partials, ctx->counter, ctx->d_state, 0);
+        }
+        ProfScope prof(ctx, RKL_K_PCG_PUPDATE, q);
         k_pupdate_z<<<g, RB, 0, ctx->stream>>>(N, ctx->zbuf, ctx->p, ctx->d_state, 0);
       }
     }

@@ -73,6 +73,7 @@ __global__ void __launch_bounds__(BLK) k_rkl2_stage(Dims d, const double *__rest
 }  // namespace
 
 int launch_apply_F(rkl_ctx *ctx, const double *u, double *Fu) {
+  ProfScope prof(ctx, RKL_K_APPLY_F);
   unsigned grid = grid_for(ctx->d.N, BLK);
   if (ctx->op == RKL_OP_CONDUCTION)
     k_apply_F<RKL_OP_CONDUCTION><<<grid, BLK, 0, ctx->stream>>>(ctx->d, ctx->coef, ctx->invW, u, Fu);
@@ -83,6 +84,7 @@ int launch_apply_F(rkl_ctx *ctx, const double *u, double *Fu) {
 }
 
 int launch_rkl2_stage1(rkl_ctx *ctx, const double *Y0, double *M0, double *Y1, double mut1dt) {
+  ProfScope prof(ctx, RKL_K_RKL2_FIRST);
   unsigned grid = grid_for(ctx->d.N, BLK);
   if (ctx->op == RKL_OP_CONDUCTION)
     k_rkl2_first<RKL_OP_CONDUCTION><<<grid, BLK, 0, ctx->stream>>>(ctx->d, ctx->coef, ctx->invW, Y0, M0,
@@ -97,6 +99,7 @@ int launch_rkl2_stage1(rkl_ctx *ctx, const double *Y0, double *M0, double *Y1, d
 int launch_rkl2_stage(rkl_ctx *ctx, const double *Ym1, const double *Ym2, const double *Y0,
                       const double *M0, double *Yout, double mu, double nu, double mutdt,
                       double gtdt) {
+  ProfScope prof(ctx, RKL_K_RKL2_STAGE);
   unsigned grid = grid_for(ctx->d.N, BLK);
   double om = 1.0 - mu - nu;
   if (ctx->op == RKL_OP_CONDUCTION)

@@ -34,7 +34,10 @@ RKL_FORCE_ODD = 1
 
 EXPORTED = ("rkl_create", "rkl_destroy", "rkl_set_stream", "rkl_strerror", "rkl_last_error",
             "rkl_kernel_launches", "rkl2_stage_count", "set_coeffs", "apply_F", "rkl2_superstep",
-            "be_pcg_solve", "rkl2_superstep_noalloc")
+            "be_pcg_solve", "rkl2_superstep_noalloc", "rkl_profile_enable", "rkl_profile_read")
+
+KERNELS = ("setup", "apply_F", "rkl2_first", "rkl2_stage", "pcg_init", "spmv", "pcg_update",
+           "pcg_pupdate", "bilu_factor", "bilu_apply")
 
 
 class RklError(RuntimeError):
@@ -83,6 +86,8 @@ def load(path: str | None = None):
     lib.rkl2_superstep.argtypes = [P, P, I, D, D, I, I, ctypes.POINTER(I)]
     lib.be_pcg_solve.argtypes = [P, P, I, D, I, ctypes.POINTER(I), D, I, P, ctypes.POINTER(I),
                                  ctypes.POINTER(D)]
+    lib.rkl_profile_enable.argtypes = [P, I]
+    lib.rkl_profile_read.argtypes = [P, I, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong)]
     lib.rkl2_superstep_noalloc.argtypes = [ctypes.POINTER(_Grid), P, P, P, D, I, P, D, I, I, P,
                                            ctypes.POINTER(D), ctypes.POINTER(I)]
     _lib = lib
@@ -201,6 +206,21 @@ class Context:
     @property
     def kernel_launches(self) -> int:
         return int(self._lib.rkl_kernel_launches(self._h))
+
+    def profile_enable(self, on: bool = True):
+        """Start (clearing the counters) or stop per-kernel event timing."""
+        self._check(self._lib.rkl_profile_enable(self._h, 1 if on else 0), "rkl_profile_enable")
+
+    def profile(self) -> dict:
+        """{kernel family: (total ms, counted launches)} (synchronises the stream)."""
+        out = {}
+        for k, name in enumerate(KERNELS):
+            ms = ctypes.c_double(0.0)
+            n = ctypes.c_longlong(0)
+            self._check(self._lib.rkl_profile_read(self._h, k, ctypes.byref(ms), ctypes.byref(n)),
+                        "rkl_profile_read")
+            out[name] = (ms.value, n.value)
+        return out
 
     def set_stream(self, stream):
         self._check(self._lib.rkl_set_stream(self._h, stream), "rkl_set_stream")
