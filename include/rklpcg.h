@@ -44,7 +44,7 @@ extern "C" {
 typedef struct rkl_ctx rkl_ctx;
 
 typedef struct {
-  int nr, nth, nph;       /* cells along r, theta, phi: nr >= 1, nth >= 1, nph >= 3 */
+  int nr, nth, nph;       /* cells along r, theta, phi: nr >= 1, 1 <= nth, 3 <= nph, both <= 65535 */
   const double *r_faces;  /* HOST array of nr+1 radial faces (R_sun), copied at create */
 } rkl_grid;
 
@@ -61,12 +61,20 @@ enum {
 
 enum { RKL_OP_CONDUCTION = 0, RKL_OP_VISCOSITY = 1 };
 enum { RKL_PC_JACOBI = 1, RKL_PC_BILU0 = 2 };
-enum { RKL_F64 = 0 };
+enum { RKL_F64 = 0, RKL_F32MIX = 1 };
 
 #define RKL_BETA_TCUT 1 /* set_coeffs: evaluate kappa at max(T, 5e5 K) (Sec. 4.1 beta_Tcut) */
 #define RKL_FORCE_ODD 1 /* rkl2_superstep: round s up to an odd number (Sec. 3) */
 
-/* Create a context for one grid on the current CUDA device.  prec must be RKL_F64.
+/* Create a context for one grid on the current CUDA device.
+ * prec = RKL_F64: every step in FP64.
+ * prec = RKL_F32MIX (mixed precision; same FP64 inputs and outputs): set_coeffs also
+ *   keeps FP32 copies of the operator; rkl2_superstep runs the stages in FP32 on the
+ *   increments Y_j - Y_0 with FP64 stage coefficients, M0 = F(Y0) in FP64 and the
+ *   result Y_0 + (Y_s - Y_0) formed in FP64; be_pcg_solve is FP64 iterative refinement
+ *   (FP64 residual and stopping test, FP32 PCG correction solves with FP64 dot
+ *   products, FP64 update), so it meets the same rtol; iters_out then counts FP32
+ *   iterations.  apply_F stays FP64.
  * cuda_stream: a cudaStream_t (NULL = legacy default stream) on which all work of
  * this context is queued.  Allocates the geometry tables; coefficient, stage and
  * Krylov buffers are allocated on first use and kept until rkl_destroy. */
@@ -138,6 +146,26 @@ int apply_F(rkl_ctx *ctx, const double *u, double *Fu, int ncomp);
  * dt <= dt_exp (s^2 + s - 2)/4, which Eq. 5 guarantees when dt_exp is set_coeffs'. */
 int rkl2_superstep(rkl_ctx *ctx, double *u, int ncomp, double dt, double dt_exp, int s,
                    int flags, int *s_used);
+
+/* Damping variants of the super-step discussed in Sec. 6: an explicit-Euler prefix over
+ * a fraction of dt (sub-steps no larger than dt_exp), then `cycles` equal sub-cycles of
+ * RKL2 (or of first-order RKL1), each with the minimal stable number of stages plus
+ * `extra_stages`.  euler_fraction = 0, cycles = 1, extra_stages = 0 and RKL2 is exactly
+ * rkl2_superstep with s from Eq. 5. */
+enum { RKL_SCHEME_RKL2 = 0, RKL_SCHEME_RKL1 = 1 };
+typedef struct {
+  int scheme;             /* RKL_SCHEME_RKL2 or RKL_SCHEME_RKL1 */
+  int cycles;             /* sub-cycles of the super-time-stepping part, >= 1 */
+  int extra_stages;       /* stages beyond the minimal stable count, >= 0 */
+  double euler_fraction;  /* leading fraction of dt taken by explicit Euler, in [0, 1) */
+  int flags;              /* RKL_FORCE_ODD (RKL2 stage counts) */
+} rkl_sts_options;
+
+/* In place u <- advance by dt with the variant in *opt (FP64 kernels, any context
+ * precision).  stages_used (host, may be NULL) receives the total number of operator
+ * applications (Euler sub-steps + stages of all cycles). */
+int sts_advance(rkl_ctx *ctx, double *u, int ncomp, double dt, double dt_exp,
+                const rkl_sts_options *opt, int *stages_used);
 
 /* In place backward-Euler step (Eqs. 2-4): solve (W + dt S) x = W u for each
  * component by PCG (Fig. 1), from x0 (or from u when x0 is NULL), stopping when

@@ -64,6 +64,9 @@ def _load():
             lib.or_rkl2_stages.argtypes = [D, I]
             lib.or_rkl2_coeffs.argtypes = [I, P, P, P, P]
             lib.or_rkl2_superstep.argtypes = [I, I, I, P, P, P, P, D, I]
+            lib.or_rkl1_stages.argtypes = [D]
+            lib.or_rkl1_coeffs.argtypes = [I, P, P, P]
+            lib.or_rkl1_superstep.argtypes = [I, I, I, P, P, P, P, D, I]
             lib.or_bilu0_factor.argtypes = [I, I, I, P, P, I, P, P]
             lib.or_bilu0_apply.argtypes = [I, I, I, P, P, I, P, P, P]
             lib.or_be_pcg.argtypes = [I, I, I, P, P, P, P, D, I, P, I, D, I, P, I, P, P]
@@ -177,6 +180,31 @@ def rkl2_superstep(g: Grid, S, W, u, dt: float, s: int) -> np.ndarray:
     if rc != 0:
         raise ValueError("s must be >= 2")
     return out
+
+
+def rkl1_stages(ratio: float) -> int:
+    """Smallest s with (s^2 + s)/2 >= dt/dt_E (at least 1)."""
+    return _load().or_rkl1_stages(float(ratio))
+
+
+def rkl1_coeffs(s: int):
+    """(mu, nu, mu~) of RKL1 indexed by stage j = 0..s."""
+    arrs = [np.zeros(s + 1) for _ in range(3)]
+    _load().or_rkl1_coeffs(int(s), *[_ptr(a) for a in arrs])
+    return tuple(arrs)
+
+
+def rkl1_superstep(g: Grid, S, W, u, dt: float, s: int) -> np.ndarray:
+    S, W = _f64(S), _f64(W)
+    out = _f64(u).copy()
+    if _load().or_rkl1_superstep(*g._dims(), _ptr(S), _ptr(W), _ptr(out), float(dt), int(s)) != 0:
+        raise ValueError("s must be >= 1")
+    return out
+
+
+def euler_step(g: Grid, S, W, u, h: float) -> np.ndarray:
+    """One explicit Euler step u + h F(u)."""
+    return _f64(u) + h * apply_F(g, S, W, u)
 
 
 def build_A(S, W, dt: float) -> np.ndarray:

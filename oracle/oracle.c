@@ -430,6 +430,55 @@ int or_rkl2_superstep(int nr, int nth, int nph, const double *rf, const double *
   return 0;
 }
 
+/* ---------------- Sec. 6: first-order RKL1 (its remark on extra stages) ----------------
+ * Y_1 = Y_0 + mu~_1 dt M Y_0,  Y_j = mu_j Y_{j-1} + nu_j Y_{j-2} + mu~_j dt M Y_{j-1},
+ * mu_j = (2j-1)/j, nu_j = -(j-1)/j, mu~_j = w1 mu_j, w1 = 2/(s^2+s); stable for
+ * dt <= dt_E (s^2+s)/2. */
+int or_rkl1_stages(double ratio) {
+  double s = ceil((sqrt(1.0 + 8.0 * ratio) - 1.0) / 2.0);
+  int si = (int)s;
+  return si < 1 ? 1 : si;
+}
+
+void or_rkl1_coeffs(int s, double *mu, double *nu, double *mut) {
+  double w1 = 2.0 / ((double)s * s + s);
+  for (int j = 0; j <= s; j++) mu[j] = nu[j] = mut[j] = 0.0;
+  mut[1] = w1;
+  for (int j = 2; j <= s; j++) {
+    mu[j] = (2.0 * j - 1.0) / j;
+    nu[j] = -(j - 1.0) / j;
+    mut[j] = w1 * mu[j];
+  }
+}
+
+int or_rkl1_superstep(int nr, int nth, int nph, const double *rf, const double *S,
+                      const double *W, double *u, double dt, int s) {
+  grid g = {nr, nth, nph, rf};
+  long N = ncell(&g);
+  if (s < 1) return -1;
+  double *mu = malloc(sizeof(double) * (s + 1)), *nu = malloc(sizeof(double) * (s + 1));
+  double *mut = malloc(sizeof(double) * (s + 1));
+  double *Ya = malloc(sizeof(double) * N), *Yb = malloc(sizeof(double) * N);
+  double *Fy = malloc(sizeof(double) * N);
+  or_rkl1_coeffs(s, mu, nu, mut);
+  or_apply_F(nr, nth, nph, rf, S, W, u, Fy);
+  for (long c = 0; c < N; c++) {
+    Yb[c] = u[c];
+    Ya[c] = u[c] + mut[1] * dt * Fy[c];
+  }
+  for (int j = 2; j <= s; j++) {
+    or_apply_F(nr, nth, nph, rf, S, W, Ya, Fy);
+    for (long c = 0; c < N; c++) {
+      double y = mu[j] * Ya[c] + nu[j] * Yb[c] + mut[j] * dt * Fy[c];
+      Yb[c] = Ya[c];
+      Ya[c] = y;
+    }
+  }
+  memcpy(u, Ya, sizeof(double) * N);
+  free(mu); free(nu); free(mut); free(Ya); free(Yb); free(Fy);
+  return 0;
+}
+
 /* ---------------- Sec. 2 / App. A: BE + PCG ---------------- */
 /* A = W + dt S in 19-slot rows */
 static void build_A(const grid *g, const double *S, const double *W, double dt, double *A) {

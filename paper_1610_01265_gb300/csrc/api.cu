@@ -31,6 +31,11 @@ int ensure_buffer(rkl_ctx *ctx, double **buf, size_t count, const char *what) {
   return cuda_check(ctx, cudaMalloc((void **)buf, count * sizeof(double)), what);
 }
 
+int ensure_fbuffer(rkl_ctx *ctx, float **buf, size_t count, const char *what) {
+  if (*buf) return RKL_OK;
+  return cuda_check(ctx, cudaMalloc((void **)buf, count * sizeof(float)), what);
+}
+
 }  // namespace rkl
 
 using namespace rkl;
@@ -183,8 +188,9 @@ int rkl2_stage_count(double ratio, int flags) {
 int rkl_create(rkl_ctx **out, const rkl_grid *g, int prec, void *stream) {
   if (!out) return RKL_EINVAL;
   *out = nullptr;
-  if (!g || !g->r_faces || prec != RKL_F64) return RKL_EINVAL;
+  if (!g || !g->r_faces || (prec != RKL_F64 && prec != RKL_F32MIX)) return RKL_EINVAL;
   if (g->nr < 1 || g->nth < 1 || g->nph < 3) return RKL_EINVAL;
+  if (g->nth > 65535 || g->nph > 65535) return RKL_EINVAL;  // 3-D launches put (j, k) on the grid
   if ((long long)g->nr * g->nth * g->nph > (1LL << 40)) return RKL_EINVAL;
   for (int i = 0; i <= g->nr; i++) {
     if (!finite_pos(g->r_faces[i])) return RKL_EINVAL;
@@ -199,6 +205,7 @@ int rkl_create(rkl_ctx **out, const rkl_grid *g, int prec, void *stream) {
   ctx->d.N = ctx->d.nrt * g->nph;
   ctx->rf.assign(g->r_faces, g->r_faces + g->nr + 1);
   ctx->stream = (cudaStream_t)stream;
+  ctx->prec = prec;
   int rc = cuda_check(ctx, cudaGetDevice(&ctx->device), "cudaGetDevice");
   if (!rc) rc = cuda_check(ctx, cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, ctx->device), "SM count");
   if (!rc) rc = build_geometry(ctx);
@@ -237,6 +244,10 @@ int rkl_destroy(rkl_ctx *ctx) {
   if (ctx->d_state) cudaFree(ctx->d_state);
   if (ctx->h_state) cudaFreeHost(ctx->h_state);
   if (ctx->plan_buf) cudaFree(ctx->plan_buf);
+  float *fbufs[] = {ctx->coef32, ctx->W32, ctx->invW32, ctx->M0f, ctx->da32, ctx->db32, ctx->r32, ctx->p32,
+                    ctx->y32, ctx->z32, ctx->e32, ctx->dinv32, ctx->LU32};
+  for (float *b : fbufs)
+    if (b) cudaFree(b);
   delete ctx;
   return RKL_OK;
 }
@@ -297,6 +308,18 @@ int set_coeffs(rkl_ctx *ctx, int op, const double *a, const double *b, const dou
     ctx->op = -1;
     return set_error(ctx, RKL_ECUDA, "set_coeffs: internal stencil assembly error");
   }
+  if (ctx->prec == RKL_F32MIX) {  // FP32 copies of the frozen operator
+    const long long nslot = op == RKL_OP_CONDUCTION ? NCOEF_COND : NCOEF_VISC;
+    if ((rc = ensure_fbuffer(ctx, &ctx->coef32, NCOEF_COND * N, "alloc FP32 coefficients")) ||
+        (rc = ensure_fbuffer(ctx, &ctx->W32, N, "alloc FP32 W")) ||
+        (rc = ensure_fbuffer(ctx, &ctx->invW32, N, "alloc FP32 1/W")) ||
+        (rc = launch_to_float(ctx, ctx->coef, ctx->coef32, nslot * (long long)N)) ||
+        (rc = launch_to_float(ctx, ctx->W, ctx->W32, (long long)N)) ||
+        (rc = launch_to_float(ctx, ctx->invW, ctx->invW32, (long long)N))) {
+      ctx->op = -1;
+      return rc;
+    }
+  }
   ctx->dt_exp = lam > 0.0 ? 2.0 / lam : INFINITY;
   if (dt_exp_out) *dt_exp_out = ctx->dt_exp;
   return RKL_OK;
@@ -342,6 +365,36 @@ int rkl2_superstep(rkl_ctx *ctx, double *u, int ncomp, double dt, double dt_exp,
   if (!is_device_ptr(u) && (rc = ensure_stage(ctx, tot))) return rc;
   if ((rc = to_device(ctx, u, tot, 0, true, &du, &su))) return rc;
   const double w1 = 4.0 / ((double)s * s + s - 2.0);
+  if (ctx->prec == RKL_F32MIX) {
+    if ((rc = ensure_fbuffer(ctx, &ctx->M0f, N, "alloc M0 (FP32)")) ||
+        (rc = ensure_fbuffer(ctx, &ctx->da32, N, "alloc increments")) ||
+        (rc = ensure_fbuffer(ctx, &ctx->db32, N, "alloc increments")))
+      return rc;
+    for (int q = 0; q < ncomp; q++) {
+      double *Y0 = du + q * N;
+      if ((rc = launch_rkl2_first_mix(ctx, Y0, ctx->M0f, ctx->da32, w1 / 3.0 * dt))) return rc;
+      float *dm1 = ctx->da32, *dm2 = nullptr;
+      for (int j = 2; j <= s; j++) {
+        double mu = (2.0 * j - 1.0) / j * rkl_b(j) / rkl_b(j - 1);
+        double nu = -(j - 1.0) / j * rkl_b(j) / rkl_b(j - 2);
+        double mut = w1 * mu;
+        double gt = -(1.0 - rkl_b(j - 1)) * mut;
+        const bool last = j == s;
+        float *out = last ? nullptr : (j == 2 ? ctx->db32 : dm2);
+        if ((rc = launch_rkl2_stage_mix(ctx, dm1, dm2, ctx->M0f, out, last ? Y0 : nullptr, mu, nu, mut * dt,
+                                        (mut + gt) * dt)))
+          return rc;
+        dm2 = dm1;
+        dm1 = out;
+      }
+    }
+    if (s_used) *s_used = s;
+    if (su) {
+      if ((rc = from_device(ctx, u, du, tot))) return rc;
+      return sync(ctx, "rkl2_superstep");
+    }
+    return RKL_OK;
+  }
   for (int q = 0; q < ncomp; q++) {
     double *Y0 = du + q * N;
     if ((rc = launch_rkl2_stage1(ctx, Y0, ctx->M0, ctx->Ya, w1 / 3.0 * dt))) return rc;
@@ -361,6 +414,91 @@ int rkl2_superstep(rkl_ctx *ctx, double *u, int ncomp, double dt, double dt_exp,
   if (su) {
     if ((rc = from_device(ctx, u, du, tot))) return rc;
     return sync(ctx, "rkl2_superstep");
+  }
+  return RKL_OK;
+}
+
+namespace {
+
+// s FP64 stages of RKL2 (scheme 0) or RKL1 (scheme 1) over dt, in place on Y0
+int run_sts(rkl_ctx *ctx, double *Y0, int scheme, int s, double dt) {
+  const bool rkl1 = scheme == RKL_SCHEME_RKL1;
+  const double w1 = rkl1 ? 2.0 / ((double)s * s + s) : 4.0 / ((double)s * s + s - 2.0);
+  int rc;
+  if (s == 1) {  // RKL1 with one stage: explicit Euler, Y1 = Y0 + w1 dt M Y0 (w1 = 1)
+    if ((rc = launch_rkl2_stage1(ctx, Y0, ctx->M0, ctx->Ya, w1 * dt))) return rc;
+    return cuda_check(ctx, cudaMemcpyAsync(Y0, ctx->Ya, sizeof(double) * ctx->d.N, cudaMemcpyDeviceToDevice,
+                                           ctx->stream), "stage copy");
+  }
+  if ((rc = launch_rkl2_stage1(ctx, Y0, ctx->M0, ctx->Ya, (rkl1 ? w1 : w1 / 3.0) * dt))) return rc;
+  double *ym1 = ctx->Ya, *ym2 = Y0;
+  for (int j = 2; j <= s; j++) {
+    double mu, nu, mut, gt;
+    if (rkl1) {
+      mu = (2.0 * j - 1.0) / j;
+      nu = -(j - 1.0) / j;
+      mut = w1 * mu;
+      gt = 0.0;
+    } else {
+      mu = (2.0 * j - 1.0) / j * rkl_b(j) / rkl_b(j - 1);
+      nu = -(j - 1.0) / j * rkl_b(j) / rkl_b(j - 2);
+      mut = w1 * mu;
+      gt = -(1.0 - rkl_b(j - 1)) * mut;
+    }
+    double *out = (j == s) ? Y0 : (j == 2 ? ctx->Yb : ym2);
+    if ((rc = launch_rkl2_stage(ctx, ym1, ym2, Y0, ctx->M0, out, mu, nu, mut * dt, gt * dt))) return rc;
+    ym2 = ym1;
+    ym1 = out;
+  }
+  return RKL_OK;
+}
+
+}  // namespace
+
+int sts_advance(rkl_ctx *ctx, double *u, int ncomp, double dt, double dt_exp, const rkl_sts_options *opt,
+                int *stages_used) {
+  if (!ctx) return RKL_EINVAL;
+  if (!u || !opt || ncomp < 1 || ncomp > 3 || !(std::isfinite(dt) && dt > 0.0) || !(dt_exp > 0.0) ||
+      (opt->scheme != RKL_SCHEME_RKL2 && opt->scheme != RKL_SCHEME_RKL1) || opt->cycles < 1 ||
+      opt->cycles > 100000 || opt->extra_stages < 0 || opt->extra_stages > 100000 ||
+      !(opt->euler_fraction >= 0.0 && opt->euler_fraction < 1.0))
+    return set_error(ctx, RKL_EINVAL, "sts_advance: bad arguments");
+  if (ctx->op < 0) return set_error(ctx, RKL_ESTATE, "sts_advance before set_coeffs");
+  const size_t N = (size_t)ctx->d.N, tot = N * ncomp;
+  int rc;
+  if ((rc = ensure_buffer(ctx, &ctx->M0, N, "alloc M0")) || (rc = ensure_buffer(ctx, &ctx->Ya, N, "alloc Y")) ||
+      (rc = ensure_buffer(ctx, &ctx->Yb, N, "alloc Y")))
+    return rc;
+  double *du;
+  bool su;
+  if (!is_device_ptr(u) && (rc = ensure_stage(ctx, tot))) return rc;
+  if ((rc = to_device(ctx, u, tot, 0, true, &du, &su))) return rc;
+  // explicit Euler prefix: n_E sub-steps of h <= dt_exp covering euler_fraction * dt
+  const double te = opt->euler_fraction * dt;
+  const long long ne = te > 0.0 ? (long long)std::ceil(te / dt_exp) : 0;
+  if (ne > 10000000) return set_error(ctx, RKL_EINVAL, "sts_advance: too many Euler sub-steps");
+  const double tau = (dt - te) / opt->cycles;
+  int s;
+  if (opt->scheme == RKL_SCHEME_RKL2) {
+    s = std::isinf(dt_exp) ? 2 : rkl2_stage_count(tau / dt_exp, 0);
+    if (s < 0) return set_error(ctx, RKL_EINVAL, "sts_advance: stage count out of range");
+    s += opt->extra_stages;
+    if ((opt->flags & RKL_FORCE_ODD) && s % 2 == 0) s++;
+  } else {
+    const double r1 = tau / dt_exp;
+    s = std::max(1, (int)std::ceil((std::sqrt(1.0 + 8.0 * r1) - 1.0) / 2.0)) + opt->extra_stages;
+  }
+  for (int q = 0; q < ncomp; q++) {
+    double *Y0 = du + q * N;
+    for (long long e = 0; e < ne; e++)
+      if ((rc = run_sts(ctx, Y0, RKL_SCHEME_RKL1, 1, te / ne))) return rc;
+    for (int cyc = 0; cyc < opt->cycles; cyc++)
+      if ((rc = run_sts(ctx, Y0, opt->scheme, s, tau))) return rc;
+  }
+  if (stages_used) *stages_used = (int)std::min<long long>(ne + (long long)opt->cycles * s, INT32_MAX);
+  if (su) {
+    if ((rc = from_device(ctx, u, du, tot))) return rc;
+    return sync(ctx, "sts_advance");
   }
   return RKL_OK;
 }

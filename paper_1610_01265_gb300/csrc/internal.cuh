@@ -120,6 +120,17 @@ struct rkl_ctx {
   // RKL2
   double *M0 = nullptr, *Ya = nullptr, *Yb = nullptr;
 
+  // mixed precision (prec == RKL_F32MIX): FP32 copies of the frozen operator and FP32
+  // work fields
+  int prec = RKL_F64;
+  float *coef32 = nullptr, *W32 = nullptr, *invW32 = nullptr;
+  float *M0f = nullptr, *da32 = nullptr, *db32 = nullptr;
+  float *r32 = nullptr, *p32 = nullptr, *y32 = nullptr, *z32 = nullptr, *e32 = nullptr,
+        *dinv32 = nullptr;
+  float *LU32 = nullptr;
+  size_t lu32_cap = 0;
+  double inner_rtol = 1e-4;
+
   // PCG
   double *r = nullptr, *p = nullptr, *y = nullptr, *zbuf = nullptr, *dinv = nullptr;
   double *partials = nullptr;
@@ -171,6 +182,7 @@ void prof_release(rkl_ctx *ctx);
 int set_error(rkl_ctx *ctx, int code, const std::string &msg);
 int cuda_check(rkl_ctx *ctx, cudaError_t e, const char *what);
 int ensure_buffer(rkl_ctx *ctx, double **buf, size_t count, const char *what);
+int ensure_fbuffer(rkl_ctx *ctx, float **buf, size_t count, const char *what);
 
 inline unsigned int grid_for(long long n, int block) {
   return (unsigned int)((n + block - 1) / block);
@@ -202,6 +214,11 @@ int launch_rkl2_stage_raw(const Dims &d, cudaStream_t stream, const double *coef
                           const double *invW, const double *Ym1, const double *Ym2,
                           const double *Y0, const double *M0, double *Yout, double mu, double nu,
                           double mutdt, double gtdt);
+
+int launch_to_float(rkl_ctx *ctx, const double *a, float *b, long long n);
+int launch_rkl2_first_mix(rkl_ctx *ctx, const double *Y0, float *M0f, float *d1, double mut1dt);
+int launch_rkl2_stage_mix(rkl_ctx *ctx, const float *dm1, const float *dm2, const float *M0f,
+                          float *dout, double *u, double mu, double nu, double mutdt, double cm0);
 
 // pcg.cu
 int pcg_solve_component(rkl_ctx *ctx, double *x, const double *u, const double *x0, double dt,

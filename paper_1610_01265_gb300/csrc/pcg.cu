@@ -102,7 +102,7 @@ __device__ void finalize_dots(PcgState *st, double rz, double rn, bool init) {
   else st->beta = rz / rold;
 }
 
-// r0 = W u - (W x0 + dt S x0); ||W u||^2; Jacobi diagonal 1/(W + dt S_cc)
+// r0 = W u - (W x0 + dt S x0); ||W u||^2 and ||r0||^2; Jacobi diagonal 1/(W + dt S_cc)
 template <int OP>
 __global__ void __launch_bounds__(RB) k_r0(Dims d, const double *__restrict__ coef,
                                            const double *__restrict__ W, double dt,
@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(RB) k_r0(Dims d, const double *__restrict__ co
                                            double *__restrict__ r, double *__restrict__ dinv,
                                            double *partials, unsigned int *counter,
                                            PcgState *st) {
-  double v[1] = {0.0};
+  double v[2] = {0.0, 0.0};
   for (long long c = (long long)blockIdx.x * RB + threadIdx.x; c < d.N; c += (long long)gridDim.x * RB) {
     int i, j, k;
     cell_coords(d, c, i, j, k);
@@ -118,35 +118,44 @@ __global__ void __launch_bounds__(RB) k_r0(Dims d, const double *__restrict__ co
     double w = W[c];
     double ax = fma(w, x0[c], dt * S_apply<OP>(d, coef, x0, c, n));
     double b = w * u[c];
-    r[c] = b - ax;
+    const double rv = b - ax;
+    r[c] = rv;
     if (dinv) dinv[c] = 1.0 / fma(dt, S_diag<OP>(d, coef, c), w);
     v[0] = fma(b, b, v[0]);
+    v[1] = fma(rv, rv, v[1]);
   }
-  double tot[1];
-  if (grid_sum<1, RB>(v, partials, counter, tot) && threadIdx.x == 0) st->bnorm2 = tot[0];
+  double tot[2];
+  if (grid_sum<2, RB>(v, partials, counter, tot) && threadIdx.x == 0) {
+    st->bnorm2 = tot[0];
+    st->rnorm2 = tot[1];
+  }
 }
 
-__global__ void __launch_bounds__(RB) k_jacobi_init(long long N, const double *__restrict__ r,
-                                                    const double *__restrict__ dinv,
-                                                    double *__restrict__ p, double *partials,
+// Iteration kernels are templated on the field type T: double for the FP64 solve, float
+// for the inner solve of the mixed-precision path.  Dot products always accumulate in
+// FP64 and the iteration scalars (alpha, beta, norms) are FP64.
+template <typename T>
+__global__ void __launch_bounds__(RB) k_jacobi_init(long long N, const T *__restrict__ r,
+                                                    const T *__restrict__ dinv,
+                                                    T *__restrict__ p, double *partials,
                                                     unsigned int *counter, PcgState *st) {
   double v[2] = {0.0, 0.0};
   for (long long c = (long long)blockIdx.x * RB + threadIdx.x; c < N; c += (long long)gridDim.x * RB) {
-    double rv = r[c], z = rv * dinv[c];
+    const T rv = r[c], z = rv * dinv[c];
     p[c] = z;
-    v[0] = fma(rv, z, v[0]);
-    v[1] = fma(rv, rv, v[1]);
+    v[0] = fma((double)rv, (double)z, v[0]);
+    v[1] = fma((double)rv, (double)rv, v[1]);
   }
   double tot[2];
   if (grid_sum<2, RB>(v, partials, counter, tot) && threadIdx.x == 0) finalize_dots(st, tot[0], tot[1], true);
 }
 
 // y = A p = W p + dt S p ; alpha = r.z / p.y
-template <int OP>
-__global__ void __launch_bounds__(RB) k_spmv(Dims d, const double *__restrict__ coef,
-                                             const double *__restrict__ W, double dt,
-                                             const double *__restrict__ p,
-                                             double *__restrict__ y, double *partials,
+template <int OP, typename T>
+__global__ void __launch_bounds__(RB) k_spmv(Dims d, const T *__restrict__ coef,
+                                             const T *__restrict__ W, T dt,
+                                             const T *__restrict__ p,
+                                             T *__restrict__ y, double *partials,
                                              unsigned int *counter, PcgState *st) {
   if (st->status != PCG_RUNNING) return;
   double v[1] = {0.0};
@@ -154,10 +163,10 @@ __global__ void __launch_bounds__(RB) k_spmv(Dims d, const double *__restrict__ 
     int i, j, k;
     cell_coords(d, c, i, j, k);
     Nbr n = neighbours(d, i, j, k);
-    double pc = p[c];
-    double yv = fma(W[c], pc, dt * S_apply<OP>(d, coef, p, c, n));
+    const T pc = p[c];
+    const T yv = fma(W[c], pc, dt * S_apply<OP, T>(d, coef, p, c, n));
     y[c] = yv;
-    v[0] = fma(pc, yv, v[0]);
+    v[0] = fma((double)pc, (double)yv, v[0]);
   }
   double tot[1];
   if (grid_sum<1, RB>(v, partials, counter, tot) && threadIdx.x == 0) {
@@ -169,58 +178,86 @@ __global__ void __launch_bounds__(RB) k_spmv(Dims d, const double *__restrict__ 
 }
 
 // x += alpha p ; r -= alpha y ; z = r / diag(A) ; r.z, r.r
-__global__ void __launch_bounds__(RB) k_update_jacobi(long long N, double *__restrict__ x,
-                                                      const double *__restrict__ p,
-                                                      double *__restrict__ r,
-                                                      const double *__restrict__ y,
-                                                      const double *__restrict__ dinv,
+template <typename T>
+__global__ void __launch_bounds__(RB) k_update_jacobi(long long N, T *__restrict__ x,
+                                                      const T *__restrict__ p,
+                                                      T *__restrict__ r,
+                                                      const T *__restrict__ y,
+                                                      const T *__restrict__ dinv,
                                                       double *partials, unsigned int *counter,
                                                       PcgState *st) {
   if (st->status != PCG_RUNNING) return;
-  const double a = st->alpha;
+  const T a = (T)st->alpha;
   double v[2] = {0.0, 0.0};
   for (long long c = (long long)blockIdx.x * RB + threadIdx.x; c < N; c += (long long)gridDim.x * RB) {
     x[c] = fma(a, p[c], x[c]);
-    double rv = fma(-a, y[c], r[c]);
+    const T rv = fma(-a, y[c], r[c]);
     r[c] = rv;
-    double z = rv * dinv[c];
-    v[0] = fma(rv, z, v[0]);
-    v[1] = fma(rv, rv, v[1]);
+    const T z = rv * dinv[c];
+    v[0] = fma((double)rv, (double)z, v[0]);
+    v[1] = fma((double)rv, (double)rv, v[1]);
   }
   double tot[2];
   if (grid_sum<2, RB>(v, partials, counter, tot) && threadIdx.x == 0) finalize_dots(st, tot[0], tot[1], false);
 }
 
-__global__ void __launch_bounds__(RB) k_pupdate_jacobi(long long N, const double *__restrict__ r,
-                                                       const double *__restrict__ dinv,
-                                                       double *__restrict__ p,
+template <typename T>
+__global__ void __launch_bounds__(RB) k_pupdate_jacobi(long long N, const T *__restrict__ r,
+                                                       const T *__restrict__ dinv,
+                                                       T *__restrict__ p,
                                                        const PcgState *st) {
   if (st->status != PCG_RUNNING) return;
-  const double b = st->beta;
+  const T b = (T)st->beta;
   for (long long c = (long long)blockIdx.x * RB + threadIdx.x; c < N; c += (long long)gridDim.x * RB)
     p[c] = fma(b, p[c], r[c] * dinv[c]);
 }
 
-__global__ void __launch_bounds__(RB) k_xr_update(long long N, double *__restrict__ x,
-                                                  const double *__restrict__ p,
-                                                  double *__restrict__ r,
-                                                  const double *__restrict__ y,
+template <typename T>
+__global__ void __launch_bounds__(RB) k_xr_update(long long N, T *__restrict__ x,
+                                                  const T *__restrict__ p,
+                                                  T *__restrict__ r,
+                                                  const T *__restrict__ y,
                                                   const PcgState *st) {
   if (st->status != PCG_RUNNING) return;
-  const double a = st->alpha;
+  const T a = (T)st->alpha;
   for (long long c = (long long)blockIdx.x * RB + threadIdx.x; c < N; c += (long long)gridDim.x * RB) {
     x[c] = fma(a, p[c], x[c]);
     r[c] = fma(-a, y[c], r[c]);
   }
 }
 
-__global__ void __launch_bounds__(RB) k_pupdate_z(long long N, const double *__restrict__ z,
-                                                  double *__restrict__ p, const PcgState *st,
+template <typename T>
+__global__ void __launch_bounds__(RB) k_pupdate_z(long long N, const T *__restrict__ z,
+                                                  T *__restrict__ p, const PcgState *st,
                                                   int first) {
   if (st->status != PCG_RUNNING) return;
-  const double b = first ? 0.0 : st->beta;
+  const T b = first ? T(0) : (T)st->beta;
   for (long long c = (long long)blockIdx.x * RB + threadIdx.x; c < N; c += (long long)gridDim.x * RB)
     p[c] = first ? z[c] : fma(b, p[c], z[c]);
+}
+
+// mixed precision: the FP64 residual r scaled by 1/sigma into the FP32 right-hand side of
+// the correction solve, whose starting guess is e = 0; ||r/sigma||^2 is the inner ||b||^2
+__global__ void __launch_bounds__(RB) k_scale_to_f32(long long N, const double *__restrict__ r,
+                                                     double inv_sigma, float *__restrict__ r32,
+                                                     float *__restrict__ e32, double *partials,
+                                                     unsigned int *counter, PcgState *st) {
+  double v[1] = {0.0};
+  for (long long c = (long long)blockIdx.x * RB + threadIdx.x; c < N; c += (long long)gridDim.x * RB) {
+    const float rv = (float)(r[c] * inv_sigma);
+    r32[c] = rv;
+    e32[c] = 0.0f;
+    v[0] = fma((double)rv, (double)rv, v[0]);
+  }
+  double tot[1];
+  if (grid_sum<1, RB>(v, partials, counter, tot) && threadIdx.x == 0) st->bnorm2 = tot[0];
+}
+
+// x += sigma e (FP64)
+__global__ void __launch_bounds__(RB) k_correct(long long N, double *__restrict__ x, double sigma,
+                                                const float *__restrict__ e32) {
+  for (long long c = (long long)blockIdx.x * RB + threadIdx.x; c < N; c += (long long)gridDim.x * RB)
+    x[c] = fma(sigma, (double)e32[c], x[c]);
 }
 
 // ---------------- block ILU0 ----------------
@@ -339,24 +376,24 @@ __global__ void __launch_bounds__(GB) k_bilu_factor(Dims d, IluPlan pl,
 constexpr int AB = 384;
 constexpr int ILU_TAB_BYTES = 8192 * 8 + 4096 * 4 * 2 + 64 * 8;  // zs + tab + goff + base
 
-template <int OP>
+template <int OP, typename T>
 __global__ void __launch_bounds__(AB) k_bilu_apply(Dims d, IluPlan pl,
-                                                   const double *__restrict__ LU,
-                                                   const double *__restrict__ r,
-                                                   double *__restrict__ z, double *partials,
+                                                   const T *__restrict__ LU,
+                                                   const T *__restrict__ r,
+                                                   T *__restrict__ z, double *partials,
                                                    unsigned int *counter, PcgState *st,
                                                    int init) {
   if (!init && st->status != PCG_RUNNING) return;
   extern __shared__ double smem[];
   const int bs = pl.bs;
-  double *zs = smem;                                        // [G][bs] by local index
-  long long *base = (long long *)(zs + (size_t)pl.G * bs);  // [G] grid index of block origin
+  T *zs = reinterpret_cast<T *>(smem);                      // [G][bs] by local index
+  long long *base = (long long *)(smem + ((size_t)pl.G * bs * sizeof(T) + 7) / 8);  // [G]
   int *tab = (int *)(base + pl.G);                          // [bs] level order: l | mask << 12
   int *goff = tab + bs;                                     // [bs] by local index
   const int grp = blockIdx.x, b0 = grp * pl.G;
   const int gcount = min(pl.G, pl.nblocks - b0);
   const size_t gs = (size_t)pl.G * bs;
-  const double *LUg = LU + (size_t)grp * ILU_SLOTS * gs;
+  const T *LUg = LU + (size_t)grp * ILU_SLOTS * gs;
   const int tid = threadIdx.x;
 
   for (int pp = tid; pp < bs; pp += AB) {
@@ -387,7 +424,7 @@ __global__ void __launch_bounds__(AB) k_bilu_apply(Dims d, IluPlan pl,
   for (int s = 0; s < NSL; s++) dl[s] = slot_ldelta(pl, s);
 
   // ---- forward sweep: z* = r - L z* ----
-  double pre[9];
+  T pre[9];
   {
     const int nl = pl.lev_start[1] - pl.lev_start[0];
     if (tid < gcount * nl) {
@@ -398,7 +435,7 @@ __global__ void __launch_bounds__(AB) k_bilu_apply(Dims d, IluPlan pl,
   __syncthreads();
   for (int lev = 0; lev < pl.nlev; lev++) {
     const int ls = pl.lev_start[lev], nl = pl.lev_start[lev + 1] - ls;
-    double cur[9];
+    T cur[9];
 #pragma unroll
     for (int s = 0; s < 9; s++) cur[s] = pre[s];
     if (lev + 1 < pl.nlev) {
@@ -412,8 +449,8 @@ __global__ void __launch_bounds__(AB) k_bilu_apply(Dims d, IluPlan pl,
     for (int q = tid; q < gcount * nl; q += AB) {
       const int bb = q / nl;
       const int t = tab[ls + (q - bb * nl)], l = t & 0xfff, mask = t >> 12;
-      double *zb = zs + bb * bs;
-      double v = zb[l];
+      T *zb = zs + bb * bs;
+      T v = zb[l];
       if (q == tid) {
 #pragma unroll
         for (int s = 1; s < 10; s++)
@@ -430,7 +467,7 @@ __global__ void __launch_bounds__(AB) k_bilu_apply(Dims d, IluPlan pl,
   }
 
   // ---- backward sweep: z = (z* - U z) / U_ii ----
-  double preb[10];
+  T preb[10];
   {
     const int lsl = pl.lev_start[pl.nlev - 1], nl = pl.lev_start[pl.nlev] - lsl;
     if (tid < gcount * nl) {
@@ -441,7 +478,7 @@ __global__ void __launch_bounds__(AB) k_bilu_apply(Dims d, IluPlan pl,
   }
   for (int lev = pl.nlev - 1; lev >= 0; lev--) {
     const int ls = pl.lev_start[lev], nl = pl.lev_start[lev + 1] - ls;
-    double cur[10];
+    T cur[10];
 #pragma unroll
     for (int s = 0; s < 10; s++) cur[s] = preb[s];
     if (lev > 0) {
@@ -455,8 +492,8 @@ __global__ void __launch_bounds__(AB) k_bilu_apply(Dims d, IluPlan pl,
     for (int q = tid; q < gcount * nl; q += AB) {
       const int bb = q / nl;
       const int t = tab[ls + (q - bb * nl)], l = t & 0xfff, mask = t >> 12;
-      double *zb = zs + bb * bs;
-      double v = zb[l];
+      T *zb = zs + bb * bs;
+      T v = zb[l];
       if (q == tid) {
 #pragma unroll
         for (int s = 10; s < NSL; s++)
@@ -476,10 +513,10 @@ __global__ void __launch_bounds__(AB) k_bilu_apply(Dims d, IluPlan pl,
   for (int q = tid; q < gcount * bs; q += AB) {
     const int bb = q / bs;
     const long long c = base[bb] + goff[q - bb * bs];
-    const double zv = zs[q], rv = r[c];
+    const T zv = zs[q], rv = r[c];
     z[c] = zv;
-    v2[0] = fma(rv, zv, v2[0]);
-    v2[1] = fma(rv, rv, v2[1]);
+    v2[0] = fma((double)rv, (double)zv, v2[0]);
+    v2[1] = fma((double)rv, (double)rv, v2[1]);
   }
   double tot[2];
   if (grid_sum<2, AB>(v2, partials, counter, tot) && threadIdx.x == 0) finalize_dots(st, tot[0], tot[1], init != 0);
@@ -550,11 +587,19 @@ int bilu0_prepare(rkl_ctx *ctx, const int *block, double dt) {
     pl.pos_of = ctx->plan_buf + nlev + 1 + bs;
     // the attribute is per function (shared by all contexts): always allow the largest group
     const int smem = ILU_TAB_BYTES;
-    rc = cuda_check(ctx, cudaFuncSetAttribute(k_bilu_apply<RKL_OP_CONDUCTION>,
+    rc = cuda_check(ctx, cudaFuncSetAttribute(k_bilu_apply<RKL_OP_CONDUCTION, double>,
                                               cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
                     "ILU shared memory");
     if (!rc)
-      rc = cuda_check(ctx, cudaFuncSetAttribute(k_bilu_apply<RKL_OP_VISCOSITY>,
+      rc = cuda_check(ctx, cudaFuncSetAttribute(k_bilu_apply<RKL_OP_VISCOSITY, double>,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
+                      "ILU shared memory");
+    if (!rc)
+      rc = cuda_check(ctx, cudaFuncSetAttribute(k_bilu_apply<RKL_OP_CONDUCTION, float>,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
+                      "ILU shared memory");
+    if (!rc)
+      rc = cuda_check(ctx, cudaFuncSetAttribute(k_bilu_apply<RKL_OP_VISCOSITY, float>,
                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
                       "ILU shared memory");
     if (rc) return rc;
@@ -580,9 +625,119 @@ int bilu0_prepare(rkl_ctx *ctx, const int *block, double dt) {
   ctx->launches += 1;
   rc = cuda_check(ctx, cudaGetLastError(), "block-ILU0 factor launch");
   if (rc) return rc;
+  if (ctx->prec == RKL_F32MIX) {  // FP32 copy of the factors for the correction solves
+    if (need > ctx->lu32_cap) {
+      if (ctx->LU32) {
+        if ((rc = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "ILU resize"))) return rc;
+        cudaFree(ctx->LU32);
+        ctx->LU32 = nullptr;
+        ctx->lu32_cap = 0;
+      }
+      if ((rc = cuda_check(ctx, cudaMalloc(&ctx->LU32, need * sizeof(float)), "FP32 block-ILU0 factors"))) return rc;
+      ctx->lu32_cap = need;
+    }
+    if ((rc = launch_to_float(ctx, ctx->LU, ctx->LU32, (long long)need))) return rc;
+  }
   ctx->lu_valid = 1;
   ctx->lu_blk[0] = bi; ctx->lu_blk[1] = bj; ctx->lu_blk[2] = bk;
   ctx->lu_dt = dt;
+  return RKL_OK;
+}
+
+template <typename T>
+struct PcgFields {
+  T *x, *r, *p, *y, *z, *dinv;
+  const T *coef, *W, *LU;
+};
+
+static int state_upload(rkl_ctx *ctx, double rtol, int maxit) {
+  PcgState init{};
+  init.rtol2 = rtol > 0.0 ? rtol * rtol : -1.0;
+  init.maxit = maxit;
+  init.status = PCG_RUNNING;
+  *ctx->h_state = init;
+  return cuda_check(ctx, cudaMemcpyAsync(ctx->d_state, ctx->h_state, sizeof(PcgState),
+                                         cudaMemcpyHostToDevice, ctx->stream), "PCG state upload");
+}
+
+static int state_read(rkl_ctx *ctx) {
+  int rc = cuda_check(ctx, cudaMemcpyAsync(ctx->h_state, ctx->d_state, sizeof(PcgState),
+                                           cudaMemcpyDeviceToHost, ctx->stream), "PCG state read");
+  if (rc) return rc;
+  return cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "PCG iteration");
+}
+
+static size_t ilu_smem(const rkl_ctx *ctx, size_t elem) {
+  const IluPlan &pl = ctx->plan;
+  return ((elem * pl.G * pl.bs + 7) / 8) * 8 + sizeof(long long) * pl.G + 2 * sizeof(int) * pl.bs;
+}
+
+// first preconditioner application once r (and for PC1 the diagonal) is in place and
+// the state holds ||b||^2: z0 = P^-1 r0, p0 = z0, r.z, convergence test
+template <int OP, typename T>
+static void pcg_first(rkl_ctx *ctx, const PcgFields<T> &f, int pc) {
+  const Dims &d = ctx->d;
+  const unsigned g = stride_grid(ctx);
+  if (pc == RKL_PC_JACOBI) {
+    k_jacobi_init<T><<<g, RB, 0, ctx->stream>>>(d.N, f.r, f.dinv, f.p, ctx->partials, ctx->counter, ctx->d_state);
+    ctx->launches += 1;
+  } else {
+    k_bilu_apply<OP, T><<<(unsigned)ctx->plan.ngroups, AB, ilu_smem(ctx, sizeof(T)), ctx->stream>>>(
+        d, ctx->plan, f.LU, f.r, f.z, ctx->partials, ctx->counter, ctx->d_state, 1);
+    k_pupdate_z<T><<<g, RB, 0, ctx->stream>>>(d.N, f.z, f.p, ctx->d_state, 1);
+    ctx->launches += 2;
+  }
+}
+
+// Fig. 1's loop, queued in chunks of 8 iterations, until the device status leaves
+// "running" (converged, breakdown, maxit)
+template <int OP, typename T>
+static int pcg_loop(rkl_ctx *ctx, const PcgFields<T> &f, double dt, int pc, int maxit) {
+  const Dims &d = ctx->d;
+  const long long N = d.N;
+  const unsigned g = stride_grid(ctx);
+  const unsigned nblk = (unsigned)ctx->plan.ngroups;
+  const size_t smem = pc == RKL_PC_BILU0 ? ilu_smem(ctx, sizeof(T)) : 0;
+  const T tdt = (T)dt;
+  const int chunk = 8;
+  int it_prev = 0, rc;
+  for (;;) {
+    if ((rc = state_read(ctx))) return rc;
+    const PcgState &h = *ctx->h_state;
+    if (ctx->prof_on) prof_settle(ctx, h.iters - it_prev, h.status == PCG_RUNNING, true);
+    it_prev = h.iters;
+    if (h.status != PCG_RUNNING || h.iters >= maxit) break;
+    for (int q = 0; q < chunk; q++) {
+      {
+        ProfScope prof(ctx, RKL_K_SPMV, q);
+        k_spmv<OP, T><<<g, RB, 0, ctx->stream>>>(d, f.coef, f.W, tdt, f.p, f.y, ctx->partials, ctx->counter,
+                                                 ctx->d_state);
+      }
+      if (pc == RKL_PC_JACOBI) {
+        {
+          ProfScope prof(ctx, RKL_K_PCG_UPDATE, q);
+          k_update_jacobi<T><<<g, RB, 0, ctx->stream>>>(N, f.x, f.p, f.r, f.y, f.dinv, ctx->partials,
+                                                        ctx->counter, ctx->d_state);
+        }
+        ProfScope prof(ctx, RKL_K_PCG_PUPDATE, q);
+        k_pupdate_jacobi<T><<<g, RB, 0, ctx->stream>>>(N, f.r, f.dinv, f.p, ctx->d_state);
+      } else {
+        {
+          ProfScope prof(ctx, RKL_K_PCG_UPDATE, q);
+          k_xr_update<T><<<g, RB, 0, ctx->stream>>>(N, f.x, f.p, f.r, f.y, ctx->d_state);
+        }
+        {
+          ProfScope prof(ctx, RKL_K_BILU_APPLY, q);
+          k_bilu_apply<OP, T><<<nblk, AB, smem, ctx->stream>>>(d, ctx->plan, f.LU, f.r, f.z, ctx->partials,
+                                                               ctx->counter, ctx->d_state, 0);
+        }
+        ProfScope prof(ctx, RKL_K_PCG_PUPDATE, q);
+        k_pupdate_z<T><<<g, RB, 0, ctx->stream>>>(N, f.z, f.p, ctx->d_state, 0);
+      }
+    }
+    ctx->launches += (long long)chunk * (pc == RKL_PC_JACOBI ? 3 : 4);
+    if ((rc = cuda_check(ctx, cudaGetLastError(), "PCG iteration launch"))) return rc;
+  }
   return RKL_OK;
 }
 
@@ -596,82 +751,23 @@ static int pcg_run(rkl_ctx *ctx, double *x, const double *u, const double *x0, d
       (rc = ensure_buffer(ctx, &ctx->y, N, "PCG y")) || (rc = ensure_buffer(ctx, &ctx->zbuf, N, "PCG z")) ||
       (rc = ensure_buffer(ctx, &ctx->dinv, N, "PCG diag")))
     return rc;
-  PcgState init{};
-  init.rtol2 = rtol > 0.0 ? rtol * rtol : -1.0;
-  init.maxit = maxit;
-  init.status = PCG_RUNNING;
-  *ctx->h_state = init;
-  if ((rc = cuda_check(ctx, cudaMemcpyAsync(ctx->d_state, ctx->h_state, sizeof(PcgState),
-                                            cudaMemcpyHostToDevice, ctx->stream), "PCG state upload")))
-    return rc;
-  unsigned int g = stride_grid(ctx);
-  const double *xs = x0 ? x0 : u;
-  unsigned int nblk = 0;
-  size_t smem = 0;
+  if ((rc = state_upload(ctx, rtol, maxit))) return rc;
+  const unsigned g = stride_grid(ctx);
+  PcgFields<double> f{x, ctx->r, ctx->p, ctx->y, ctx->zbuf, ctx->dinv, ctx->coef, ctx->W, ctx->LU};
   {
-  ProfScope prof(ctx, RKL_K_PCG_INIT);
-  k_r0<OP><<<g, RB, 0, ctx->stream>>>(d, ctx->coef, ctx->W, dt, u, xs, ctx->r,
-                                      pc == RKL_PC_JACOBI ? ctx->dinv : nullptr, ctx->partials,
-                                      ctx->counter, ctx->d_state);
-  if (x0 && x0 != x) {
-    if ((rc = cuda_check(ctx, cudaMemcpyAsync(x, x0, sizeof(double) * N, cudaMemcpyDeviceToDevice, ctx->stream), "x0 copy")))
+    ProfScope prof(ctx, RKL_K_PCG_INIT);
+    k_r0<OP><<<g, RB, 0, ctx->stream>>>(d, ctx->coef, ctx->W, dt, u, x0 ? x0 : u, ctx->r,
+                                        pc == RKL_PC_JACOBI ? ctx->dinv : nullptr, ctx->partials,
+                                        ctx->counter, ctx->d_state);
+    ctx->launches += 1;
+    if (x0 && x0 != x &&
+        (rc = cuda_check(ctx, cudaMemcpyAsync(x, x0, sizeof(double) * N, cudaMemcpyDeviceToDevice, ctx->stream),
+                         "x0 copy")))
       return rc;
+    pcg_first<OP, double>(ctx, f, pc);
   }
-  if (pc == RKL_PC_JACOBI) {
-    k_jacobi_init<<<g, RB, 0, ctx->stream>>>(N, ctx->r, ctx->dinv, ctx->p, ctx->partials, ctx->counter, ctx->d_state);
-  } else {
-    nblk = (unsigned int)ctx->plan.ngroups;
-    smem = sizeof(double) * ctx->plan.G * ctx->plan.bs + sizeof(long long) * ctx->plan.G +
-           2 * sizeof(int) * ctx->plan.bs;
-    k_bilu_apply<OP><<<nblk, AB, smem, ctx->stream>>>(d, ctx->plan, ctx->LU, ctx->r, ctx->zbuf, ctx->partials,
-                                                      ctx->counter, ctx->d_state, 1);
-    k_pupdate_z<<<g, RB, 0, ctx->stream>>>(N, ctx->zbuf, ctx->p, ctx->d_state, 1);
-  }
-  }
-  ctx->launches += 2;
   if ((rc = cuda_check(ctx, cudaGetLastError(), "PCG init launch"))) return rc;
-  const int chunk = 8;
-  int it_prev = 0;
-  for (;;) {
-    if ((rc = cuda_check(ctx, cudaMemcpyAsync(ctx->h_state, ctx->d_state, sizeof(PcgState),
-                                              cudaMemcpyDeviceToHost, ctx->stream), "PCG state read")))
-      return rc;
-    if ((rc = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "PCG iteration"))) return rc;
-    const PcgState &h = *ctx->h_state;
-    if (ctx->prof_on) prof_settle(ctx, h.iters - it_prev, h.status == PCG_RUNNING, true);
-    it_prev = h.iters;
-    if (h.status != PCG_RUNNING || h.iters >= maxit) break;
-    for (int q = 0; q < chunk; q++) {
-      {
-        ProfScope prof(ctx, RKL_K_SPMV, q);
-        k_spmv<OP><<<g, RB, 0, ctx->stream>>>(d, ctx->coef, ctx->W, dt, ctx->p, ctx->y, ctx->partials,
-                                              ctx->counter, ctx->d_state);
-      }
-      if (pc == RKL_PC_JACOBI) {
-        {
-          ProfScope prof(ctx, RKL_K_PCG_UPDATE, q);
-          k_update_jacobi<<<g, RB, 0, ctx->stream>>>(N, x, ctx->p, ctx->r, ctx->y, ctx->dinv, ctx->partials,
-                                                     ctx->counter, ctx->d_state);
-        }
-        ProfScope prof(ctx, RKL_K_PCG_PUPDATE, q);
-        k_pupdate_jacobi<<<g, RB, 0, ctx->stream>>>(N, ctx->r, ctx->dinv, ctx->p, ctx->d_state);
-      } else {
-        {
-          ProfScope prof(ctx, RKL_K_PCG_UPDATE, q);
-          k_xr_update<<<g, RB, 0, ctx->stream>>>(N, x, ctx->p, ctx->r, ctx->y, ctx->d_state);
-        }
-        {
-          ProfScope prof(ctx, RKL_K_BILU_APPLY, q);
-          k_bilu_apply<OP><<<nblk, AB, smem, ctx->stream>>>(d, ctx->plan, ctx->LU, ctx->r, ctx->zbuf,
-                                                            ctx->partials, ctx->counter, ctx->d_state, 0);
-        }
-        ProfScope prof(ctx, RKL_K_PCG_PUPDATE, q);
-        k_pupdate_z<<<g, RB, 0, ctx->stream>>>(N, ctx->zbuf, ctx->p, ctx->d_state, 0);
-      }
-    }
-    ctx->launches += (long long)chunk * (pc == RKL_PC_JACOBI ? 3 : 4);
-    if ((rc = cuda_check(ctx, cudaGetLastError(), "PCG iteration launch"))) return rc;
-  }
+  if ((rc = pcg_loop<OP, double>(ctx, f, dt, pc, maxit))) return rc;
   const PcgState &h = *ctx->h_state;
   *iters = h.iters;
   *relres = h.bnorm2 > 0.0 ? std::sqrt(h.rnorm2 / h.bnorm2) : 0.0;
@@ -681,8 +777,96 @@ static int pcg_run(rkl_ctx *ctx, double *x, const double *u, const double *x0, d
   return RKL_OK;
 }
 
+// Mixed precision: FP64 iterative refinement around FP32 PCG.  Each outer step computes
+// the FP64 residual r = W u - (W + dt S) x and its norm, stops when ||r|| <= rtol ||W u||,
+// otherwise solves (W + dt S) e = r / sigma in FP32 (sigma = RMS of r) to the relative
+// tolerance inner_rtol and updates x += sigma e in FP64.  iters counts FP32 iterations.
+template <int OP>
+static int pcg_run_mixed(rkl_ctx *ctx, double *x, const double *u, const double *x0, double dt,
+                         int pc, double rtol, int maxit, int *iters, double *relres, int *status) {
+  const Dims &d = ctx->d;
+  const long long N = d.N;
+  int rc;
+  if ((rc = ensure_buffer(ctx, &ctx->r, N, "PCG r")) || (rc = ensure_buffer(ctx, &ctx->dinv, N, "PCG diag")) ||
+      (rc = ensure_buffer(ctx, &ctx->p, N, "copy of u^n")) ||
+      (rc = ensure_fbuffer(ctx, &ctx->r32, N, "PCG r32")) || (rc = ensure_fbuffer(ctx, &ctx->p32, N, "PCG p32")) ||
+      (rc = ensure_fbuffer(ctx, &ctx->y32, N, "PCG y32")) || (rc = ensure_fbuffer(ctx, &ctx->z32, N, "PCG z32")) ||
+      (rc = ensure_fbuffer(ctx, &ctx->e32, N, "PCG e32")) || (rc = ensure_fbuffer(ctx, &ctx->dinv32, N, "PCG d32")))
+    return rc;
+  const unsigned g = stride_grid(ctx);
+  PcgFields<float> f{ctx->e32, ctx->r32, ctx->p32, ctx->y32, ctx->z32, ctx->dinv32, ctx->coef32, ctx->W32, ctx->LU32};
+  // x may share its buffer with u: keep u^n for the right-hand side W u^n of every
+  // outer residual (the FP64 buffer p is not used by the mixed solve)
+  double *un = ctx->p;
+  if ((rc = cuda_check(ctx, cudaMemcpyAsync(un, u, sizeof(double) * N, cudaMemcpyDeviceToDevice, ctx->stream),
+                       "copy of u^n")))
+    return rc;
+  int total = 0, st = PCG_MAXIT;
+  double bn2 = 0.0, rn2 = 0.0;
+  for (int outer = 0; outer < 64; outer++) {
+    {
+      ProfScope prof(ctx, RKL_K_PCG_INIT);
+      const double *xs = outer == 0 ? (x0 ? x0 : un) : x;
+      k_r0<OP><<<g, RB, 0, ctx->stream>>>(d, ctx->coef, ctx->W, dt, un, xs, ctx->r,
+                                          outer == 0 && pc == RKL_PC_JACOBI ? ctx->dinv : nullptr,
+                                          ctx->partials, ctx->counter, ctx->d_state);
+      ctx->launches += 1;
+      if (outer == 0 && pc == RKL_PC_JACOBI && (rc = launch_to_float(ctx, ctx->dinv, ctx->dinv32, N))) return rc;
+      if (outer == 0 && x0 && x0 != x &&
+          (rc = cuda_check(ctx, cudaMemcpyAsync(x, x0, sizeof(double) * N, cudaMemcpyDeviceToDevice, ctx->stream),
+                           "x0 copy")))
+        return rc;
+    }
+    if ((rc = state_read(ctx))) return rc;
+    bn2 = ctx->h_state->bnorm2;
+    rn2 = ctx->h_state->rnorm2;
+    if (!std::isfinite(rn2) || !std::isfinite(bn2)) {
+      st = PCG_BREAKDOWN;
+      break;
+    }
+    if (rtol > 0.0 && rn2 <= rtol * rtol * bn2) {
+      st = PCG_CONVERGED;
+      break;
+    }
+    if (rn2 == 0.0) {
+      st = PCG_CONVERGED;
+      break;
+    }
+    if (total >= maxit) break;
+    const double sigma = std::sqrt(rn2 / (double)N);
+    if ((rc = state_upload(ctx, ctx->inner_rtol, maxit - total))) return rc;
+    {
+      ProfScope prof(ctx, RKL_K_PCG_INIT);
+      k_scale_to_f32<<<g, RB, 0, ctx->stream>>>(N, ctx->r, 1.0 / sigma, ctx->r32, ctx->e32, ctx->partials,
+                                                ctx->counter, ctx->d_state);
+      ctx->launches += 1;
+      pcg_first<OP, float>(ctx, f, pc);
+    }
+    if ((rc = cuda_check(ctx, cudaGetLastError(), "mixed PCG init launch"))) return rc;
+    if ((rc = pcg_loop<OP, float>(ctx, f, dt, pc, maxit - total))) return rc;
+    const PcgState &h = *ctx->h_state;
+    total += h.iters;
+    if (h.status == PCG_BREAKDOWN) {
+      st = PCG_BREAKDOWN;
+      break;
+    }
+    k_correct<<<g, RB, 0, ctx->stream>>>(N, x, sigma, ctx->e32);
+    ctx->launches += 1;
+    if ((rc = cuda_check(ctx, cudaGetLastError(), "mixed PCG correction launch"))) return rc;
+  }
+  *iters = total;
+  *relres = bn2 > 0.0 ? std::sqrt(rn2 / bn2) : 0.0;
+  *status = st;
+  return RKL_OK;
+}
+
 int pcg_solve_component(rkl_ctx *ctx, double *x, const double *u, const double *x0, double dt,
                         int pc, double rtol, int maxit, int *iters, double *relres, int *status) {
+  if (ctx->prec == RKL_F32MIX) {
+    if (ctx->op == RKL_OP_CONDUCTION)
+      return pcg_run_mixed<RKL_OP_CONDUCTION>(ctx, x, u, x0, dt, pc, rtol, maxit, iters, relres, status);
+    return pcg_run_mixed<RKL_OP_VISCOSITY>(ctx, x, u, x0, dt, pc, rtol, maxit, iters, relres, status);
+  }
   if (ctx->op == RKL_OP_CONDUCTION)
     return pcg_run<RKL_OP_CONDUCTION>(ctx, x, u, x0, dt, pc, rtol, maxit, iters, relres, status);
   return pcg_run<RKL_OP_VISCOSITY>(ctx, x, u, x0, dt, pc, rtol, maxit, iters, relres, status);

@@ -9,6 +9,8 @@
 // FP64 work per cell: 19 (stencil) + 6 (recurrence) DP instructions.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "internal.cuh"
 #include "stencil.cuh"
 
@@ -70,7 +72,94 @@ __global__ void __launch_bounds__(BLK) k_rkl2_stage(Dims d, const double *__rest
   Yout[c] = y;
 }
 
+// ---- mixed precision (FP32 stages on increments, FP64 kept where it matters) ----
+//
+// With Y_j = Y_0 + delta_j the recurrence of Fig. 2 becomes
+//   delta_j = mu_j delta_{j-1} + nu_j delta_{j-2} + mu~_j dt M delta_{j-1}
+//             + (mu~_j + gamma~_j) dt M_0,       delta_0 = 0, delta_1 = mu~_1 dt M_0,
+// because M Y_{j-1} = M_0 + M delta_{j-1}.  M_0 = M Y_0 is computed in FP64 (the large
+// values of Y_0 cancel in the stencil); the increments, the stencil on them and the
+// recurrence run in FP32; the last stage writes u = Y_0 + delta_s in FP64.
+
+template <int OP>
+__global__ void __launch_bounds__(BLK) k_rkl2_first_mix(Dims d, const double *__restrict__ coef,
+                                                        const double *__restrict__ invW,
+                                                        const double *__restrict__ Y0,
+                                                        float *__restrict__ M0f,
+                                                        float *__restrict__ d1, double mut1dt) {
+  long long c = (long long)blockIdx.x * BLK + threadIdx.x;
+  if (c >= d.N) return;
+  int i, j, k;
+  cell_coords(d, c, i, j, k);
+  Nbr n = neighbours(d, i, j, k);
+  const double m0 = -invW[c] * S_apply<OP>(d, coef, Y0, c, n);
+  M0f[c] = (float)m0;
+  d1[c] = (float)(mut1dt * m0);
+}
+
+// dm2 == nullptr stands for delta_0 = 0; u != nullptr marks the last stage (u += delta_s)
+template <int OP>
+__global__ void __launch_bounds__(BLK) k_rkl2_stage_mix(Dims d, const float *__restrict__ coef,
+                                                        const float *__restrict__ invW,
+                                                        const float *__restrict__ dm1,
+                                                        const float *dm2,
+                                                        const float *__restrict__ M0f,
+                                                        float *dout, double *u, float mu, float nu,
+                                                        float mutdt, float cm0) {
+  // 3-D launch: i from the thread, (j, k) from the grid (no index division)
+  const int i = blockIdx.x * BLK + threadIdx.x;
+  if (i >= d.nr) return;
+  const int j = blockIdx.y, k = blockIdx.z;
+  const long long c = ((long long)k * d.nth + j) * d.nr + i;
+  Nbr n = neighbours(d, i, j, k);
+  const float f = -invW[c] * S_apply<OP, float>(d, coef, dm1, c, n);
+  float y = mu * dm1[c];
+  if (dm2) y = fmaf(nu, dm2[c], y);
+  y = fmaf(mutdt, f, y);
+  y = fmaf(cm0, M0f[c], y);
+  if (u) u[c] += (double)y;
+  else dout[c] = y;
+}
+
+__global__ void __launch_bounds__(BLK) k_to_float(long long n, const double *__restrict__ a,
+                                                  float *__restrict__ b) {
+  for (long long c = (long long)blockIdx.x * BLK + threadIdx.x; c < n; c += (long long)gridDim.x * BLK)
+    b[c] = (float)a[c];
+}
+
 }  // namespace
+
+int launch_to_float(rkl_ctx *ctx, const double *a, float *b, long long n) {
+  long long g = std::min<long long>((n + BLK - 1) / BLK, (long long)ctx->nsm * 16);
+  k_to_float<<<(unsigned)std::max(1LL, g), BLK, 0, ctx->stream>>>(n, a, b);
+  ctx->launches += 1;
+  return cuda_check(ctx, cudaGetLastError(), "FP32 conversion launch");
+}
+
+int launch_rkl2_first_mix(rkl_ctx *ctx, const double *Y0, float *M0f, float *d1, double mut1dt) {
+  ProfScope prof(ctx, RKL_K_RKL2_FIRST);
+  unsigned grid = grid_for(ctx->d.N, BLK);
+  if (ctx->op == RKL_OP_CONDUCTION)
+    k_rkl2_first_mix<RKL_OP_CONDUCTION><<<grid, BLK, 0, ctx->stream>>>(ctx->d, ctx->coef, ctx->invW, Y0, M0f, d1, mut1dt);
+  else
+    k_rkl2_first_mix<RKL_OP_VISCOSITY><<<grid, BLK, 0, ctx->stream>>>(ctx->d, ctx->coef, ctx->invW, Y0, M0f, d1, mut1dt);
+  ctx->launches += 1;
+  return cuda_check(ctx, cudaGetLastError(), "mixed rkl2 stage-1 launch");
+}
+
+int launch_rkl2_stage_mix(rkl_ctx *ctx, const float *dm1, const float *dm2, const float *M0f,
+                          float *dout, double *u, double mu, double nu, double mutdt, double cm0) {
+  ProfScope prof(ctx, RKL_K_RKL2_STAGE);
+  const dim3 grid(grid_for(ctx->d.nr, BLK), (unsigned)ctx->d.nth, (unsigned)ctx->d.nph);
+  if (ctx->op == RKL_OP_CONDUCTION)
+    k_rkl2_stage_mix<RKL_OP_CONDUCTION><<<grid, BLK, 0, ctx->stream>>>(
+        ctx->d, ctx->coef32, ctx->invW32, dm1, dm2, M0f, dout, u, (float)mu, (float)nu, (float)mutdt, (float)cm0);
+  else
+    k_rkl2_stage_mix<RKL_OP_VISCOSITY><<<grid, BLK, 0, ctx->stream>>>(
+        ctx->d, ctx->coef32, ctx->invW32, dm1, dm2, M0f, dout, u, (float)mu, (float)nu, (float)mutdt, (float)cm0);
+  ctx->launches += 1;
+  return cuda_check(ctx, cudaGetLastError(), "mixed rkl2 stage launch");
+}
 
 int launch_apply_F(rkl_ctx *ctx, const double *u, double *Fu) {
   ProfScope prof(ctx, RKL_K_APPLY_F);

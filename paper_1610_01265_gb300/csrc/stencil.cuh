@@ -39,10 +39,11 @@ __device__ __forceinline__ Nbr neighbours(const Dims &d, int i, int j, int k) {
   return n;
 }
 
-// 19-point conduction operator, coef = [10][N] (9 forward + diagonal)
-__device__ __forceinline__ double S_apply_cond(const Dims &d, const double *__restrict__ coef,
-                                               const double *__restrict__ u, long long c,
-                                               const Nbr &n) {
+// 19-point conduction operator, coef = [10][N] (9 forward + diagonal); T = double, or
+// float for the mixed-precision path (FP32 coefficients and fields, FP32 accumulation)
+template <typename T>
+__device__ __forceinline__ T S_apply_cond(const Dims &d, const T *__restrict__ coef,
+                                          const T *__restrict__ u, long long c, const Nbr &n) {
   const long long N = d.N;
   const long long f[9] = {c + n.rp,        c + n.tp,        c + n.pp,
                           c + n.rm + n.tp, c + n.rp + n.tp, c + n.rm + n.pp,
@@ -52,43 +53,41 @@ __device__ __forceinline__ double S_apply_cond(const Dims &d, const double *__re
                           c + n.rm + n.pm, c + n.tp + n.pm, c + n.tm + n.pm};
   const bool bv[9] = {n.vrm, n.vtm, true, n.vrp && n.vtm, n.vrm && n.vtm,
                       n.vrp, n.vrm, n.vtp, n.vtm};
-  double acc = coef[9 * N + c] * u[c];
+  T acc = coef[9 * N + c] * u[c];
 #pragma unroll
   for (int m = 0; m < 9; m++) acc = fma(coef[m * N + c], u[f[m]], acc);
 #pragma unroll
   for (int m = 0; m < 9; m++) {
-    double cb = bv[m] ? coef[m * N + b[m]] : 0.0;
+    T cb = bv[m] ? coef[m * N + b[m]] : T(0);
     acc = fma(cb, u[b[m]], acc);
   }
   return acc;
 }
 
 // 7-point viscosity operator, coef = [4][N] (3 forward + diagonal)
-__device__ __forceinline__ double S_apply_visc(const Dims &d, const double *__restrict__ coef,
-                                               const double *__restrict__ u, long long c,
-                                               const Nbr &n) {
+template <typename T>
+__device__ __forceinline__ T S_apply_visc(const Dims &d, const T *__restrict__ coef,
+                                          const T *__restrict__ u, long long c, const Nbr &n) {
   const long long N = d.N;
-  double acc = coef[3 * N + c] * u[c];
+  T acc = coef[3 * N + c] * u[c];
   acc = fma(coef[0 * N + c], u[c + n.rp], acc);
   acc = fma(coef[1 * N + c], u[c + n.tp], acc);
   acc = fma(coef[2 * N + c], u[c + n.pp], acc);
-  acc = fma(n.vrm ? coef[0 * N + c + n.rm] : 0.0, u[c + n.rm], acc);
-  acc = fma(n.vtm ? coef[1 * N + c + n.tm] : 0.0, u[c + n.tm], acc);
+  acc = fma(n.vrm ? coef[0 * N + c + n.rm] : T(0), u[c + n.rm], acc);
+  acc = fma(n.vtm ? coef[1 * N + c + n.tm] : T(0), u[c + n.tm], acc);
   acc = fma(coef[2 * N + c + n.pm], u[c + n.pm], acc);
   return acc;
 }
 
-template <int OP>
-__device__ __forceinline__ double S_apply(const Dims &d, const double *__restrict__ coef,
-                                          const double *__restrict__ u, long long c,
-                                          const Nbr &n) {
-  if (OP == RKL_OP_CONDUCTION) return S_apply_cond(d, coef, u, c, n);
-  return S_apply_visc(d, coef, u, c, n);
+template <int OP, typename T>
+__device__ __forceinline__ T S_apply(const Dims &d, const T *__restrict__ coef,
+                                     const T *__restrict__ u, long long c, const Nbr &n) {
+  if (OP == RKL_OP_CONDUCTION) return S_apply_cond<T>(d, coef, u, c, n);
+  return S_apply_visc<T>(d, coef, u, c, n);
 }
 
-template <int OP>
-__device__ __forceinline__ double S_diag(const Dims &d, const double *__restrict__ coef,
-                                         long long c) {
+template <int OP, typename T>
+__device__ __forceinline__ T S_diag(const Dims &d, const T *__restrict__ coef, long long c) {
   return coef[(OP == RKL_OP_CONDUCTION ? 9 : 3) * d.N + c];
 }
 

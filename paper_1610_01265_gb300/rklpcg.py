@@ -29,12 +29,16 @@ RKL_OP_VISCOSITY = 1
 RKL_PC_JACOBI = 1
 RKL_PC_BILU0 = 2
 RKL_F64 = 0
+RKL_F32MIX = 1
 RKL_BETA_TCUT = 1
 RKL_FORCE_ODD = 1
 
 EXPORTED = ("rkl_create", "rkl_destroy", "rkl_set_stream", "rkl_strerror", "rkl_last_error",
             "rkl_kernel_launches", "rkl2_stage_count", "set_coeffs", "apply_F", "rkl2_superstep",
-            "be_pcg_solve", "rkl2_superstep_noalloc", "rkl_profile_enable", "rkl_profile_read")
+            "be_pcg_solve", "rkl2_superstep_noalloc", "rkl_profile_enable", "rkl_profile_read",
+            "sts_advance")
+RKL_SCHEME_RKL2 = 0
+RKL_SCHEME_RKL1 = 1
 
 KERNELS = ("setup", "apply_F", "rkl2_first", "rkl2_stage", "pcg_init", "spmv", "pcg_update",
            "pcg_pupdate", "bilu_factor", "bilu_apply")
@@ -47,6 +51,11 @@ class RklError(RuntimeError):
         if detail:
             msg += f": {detail}"
         super().__init__(msg)
+
+
+class StsOptions(ctypes.Structure):
+    _fields_ = [("scheme", ctypes.c_int), ("cycles", ctypes.c_int), ("extra_stages", ctypes.c_int),
+                ("euler_fraction", ctypes.c_double), ("flags", ctypes.c_int)]
 
 
 class _Grid(ctypes.Structure):
@@ -86,6 +95,7 @@ def load(path: str | None = None):
     lib.rkl2_superstep.argtypes = [P, P, I, D, D, I, I, ctypes.POINTER(I)]
     lib.be_pcg_solve.argtypes = [P, P, I, D, I, ctypes.POINTER(I), D, I, P, ctypes.POINTER(I),
                                  ctypes.POINTER(D)]
+    lib.sts_advance.argtypes = [P, P, I, D, D, ctypes.POINTER(StsOptions), ctypes.POINTER(I)]
     lib.rkl_profile_enable.argtypes = [P, I]
     lib.rkl_profile_read.argtypes = [P, I, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong)]
     lib.rkl2_superstep_noalloc.argtypes = [ctypes.POINTER(_Grid), P, P, P, D, I, P, D, I, I, P,
@@ -163,7 +173,9 @@ def _current_stream():
 class Context:
     """One grid on the current CUDA device; mirrors rkl_create .. rkl_destroy."""
 
-    def __init__(self, r_faces, nth: int, nph: int, stream=None):
+    def __init__(self, r_faces, nth: int, nph: int, stream=None, prec: int = RKL_F64):
+        """prec = RKL_F64, or RKL_F32MIX for the mixed-precision path (FP32 operator and
+        stages, FP64 coefficients of the recurrence, dot products and residual correction)."""
         self._lib = load()
         rf = np.ascontiguousarray(r_faces, dtype=np.float64)
         self.nr, self.nth, self.nph = len(rf) - 1, int(nth), int(nph)
@@ -173,7 +185,7 @@ class Context:
         h = ctypes.c_void_p()
         if stream is None:
             stream = _current_stream()
-        code = self._lib.rkl_create(ctypes.byref(h), ctypes.byref(g), RKL_F64, stream)
+        code = self._lib.rkl_create(ctypes.byref(h), ctypes.byref(g), int(prec), stream)
         if code != RKL_OK:
             raise RklError(code, "rkl_create")
         self._h = h
@@ -251,6 +263,19 @@ class Context:
                                         float(dt_exp), int(s), RKL_FORCE_ODD if force_odd else 0,
                                         ctypes.byref(used))
         self._check(code, "rkl2_superstep")
+        return used.value
+
+    def sts_advance(self, u, dt: float, dt_exp: float, scheme: int = RKL_SCHEME_RKL2, cycles: int = 1,
+                    extra_stages: int = 0, euler_fraction: float = 0.0, force_odd: bool = False,
+                    ncomp: int = 1) -> int:
+        """Sec. 6 damping variants (Euler prefix, sub-cycles, RKL1, extra stages); returns the
+        number of operator applications."""
+        opt = StsOptions(int(scheme), int(cycles), int(extra_stages), float(euler_fraction),
+                         RKL_FORCE_ODD if force_odd else 0)
+        used = ctypes.c_int(0)
+        code = self._lib.sts_advance(self._h, _ptr(u, self.N * ncomp), int(ncomp), float(dt), float(dt_exp),
+                                     ctypes.byref(opt), ctypes.byref(used))
+        self._check(code, "sts_advance")
         return used.value
 
     def be_pcg_solve(self, u, dt: float, pc: int = RKL_PC_JACOBI, block=(8, 8, 8), rtol: float = 1e-10,

@@ -167,3 +167,69 @@ def test_superstep_conserves_energy(oracle_mod):
     assert abs(e1 - e0) <= 1e-13 * abs(e0)
     assert np.isfinite(out).all()
     assert out.max() <= c["T"].max() * (1 + 1e-12) and out.min() >= c["T"].min() * (1 - 1e-12)
+
+
+# ---------------- RKL1 (Sec. 6 remark: extra stages damp the highest mode) ----------------
+
+def rkl1_fn(O, s, z):
+    mu, nu, mut = O.rkl1_coeffs(s)
+    Ym2 = 1.0 + 0.0 * z
+    Ym1 = Ym2 + mut[1] * z
+    for j in range(2, s + 1):
+        Y = mu[j] * Ym1 + nu[j] * Ym2 + mut[j] * z * Ym1
+        Ym2, Ym1 = Ym1, Y
+    return Ym1
+
+
+@pytest.mark.parametrize("s", [1, 2, 3, 8, 25])
+def test_rkl1_stability_polynomial(oracle_mod, s):
+    """RKL1 is built so that R_s(z) = P_s(1 + w1 z), w1 = 2/(s^2+s): first order, |R| <= 1 on
+    [-(s^2+s), 0] and |R| = 1 at its left end (no damping of the highest mode)."""
+    O = oracle_mod
+    w1 = 2.0 / (s * s + s)
+    c = rkl1_fn(O, s, np.polynomial.Polynomial([0.0, 1.0])).coef
+    assert c[0] == pytest.approx(1.0, abs=1e-13) and c[1] == pytest.approx(1.0, rel=1e-12)
+    zs = np.linspace(-(s * s + s), 0.0, 2001)
+    closed = eval_legendre(s, 1 + w1 * zs)
+    assert np.abs(rkl1_fn(O, s, zs) - closed).max() < 1e-11
+    assert np.abs(closed).max() <= 1 + 1e-12
+    assert abs(abs(closed[0]) - 1.0) < 1e-12
+
+
+def test_rkl1_extra_stages_damp_the_highest_mode(oracle_mod):
+    """With one or more stages beyond the minimum, |R| at the largest |z| the step reaches
+    drops below one (Sec. 6)."""
+    for ratio in (10.0, 100.0, 1000.0):
+        s = 1
+        while (s * s + s) / 2 < ratio:
+            s += 1
+        zmax = 2 * ratio  # dt |lambda|max = 2 dt/dt_E
+        for extra in (1, 2, 5):
+            se = s + extra
+            r = abs(eval_legendre(se, 1 - 2 * zmax / (se * se + se)))
+            assert r < 1 - 1e-3
+
+
+@pytest.mark.parametrize("ratio", [3.0, 40.0, 400.0])
+def test_rkl1_superstep_on_eigenvectors(oracle_mod, ratio):
+    O = oracle_mod
+    g, S, W, phi, one = ring_case(O)
+    dtE, _ = O.gershgorin_dt(g, S, W)
+    s = O.rkl1_stages(ratio)
+    assert (s * s + s) / 2 >= ratio and (s == 1 or ((s - 1) ** 2 + s - 1) / 2 < ratio)
+    for m in (1, 5):
+        u = np.cos(m * phi)[:, None, None] * one
+        lam = (O.apply_F(g, S, W, u) / u)[0]
+        out = O.rkl1_superstep(g, S, W, u, ratio * dtE, s + 1)
+        w1 = 2.0 / ((s + 1) ** 2 + s + 1)
+        assert np.abs(out - eval_legendre(s + 1, 1 + w1 * lam * ratio * dtE)[None] * u).max() <= 1e-12
+
+
+def test_exact_s_step_damps_the_edge_for_odd_s():
+    """Sec. 6: choosing s first and dt = dt_E (s^2+s-2)/4 exactly, the RKL2 factor at the
+    highest mode is a_s + (-1)^s b_s, which is 2/(s(s+1)) for odd s (near zero); one stage
+    more than needed for the same dt leaves it near a_s ~ 1/2 at the edge."""
+    for s in (5, 21, 45):
+        zedge = -(s * s + s - 2) / 2.0
+        assert R_closed(s, zedge) == pytest.approx(2.0 / (s * (s + 1)), rel=1e-10)
+        assert R_closed(s + 1, zedge) > 0.3
