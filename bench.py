@@ -69,7 +69,8 @@ def parse_args():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-accuracy", action="store_true")
     p.add_argument("--seed", type=int, default=1)
-    p.add_argument("--profile", choices=("stage", "apply", "pcg-jacobi", "pcg-bilu0", "setup"),
+    p.add_argument("--profile", choices=("stage", "apply", "pcg-jacobi", "pcg-bilu0", "setup", "stage-mix",
+                                         "pcg-jacobi-mix"),
                    help="run only a minimal case of one kernel family for an ncu capture (no timing)")
     return p.parse_args()
 
@@ -362,6 +363,62 @@ def path_timings(wl, torch):
     return out
 
 
+def mixed_report(wl, R, torch):
+    """Mixed precision (FP32 stages / FP32 PCG with FP64 refinement) against the FP64 GPU
+    path on the same inputs: ms per large step and error relative to the step's change."""
+    nr, nth, nph = GRID
+    out = {}
+    mix = R.Context(wl.ctx_c._rf, nth, nph, prec=R.RKL_F32MIX)
+    try:
+        dte = mix.set_conduction(wl.T, wl.b, wl.n)
+        wl.ctx_c.set_conduction(wl.T, wl.b, wl.n)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ref = torch.empty_like(wl.T)
+        for ratio in RATIOS:
+            ref.copy_(wl.T)
+            wl.ctx_c.rkl2_superstep(ref, ratio * dte, dte)
+            wl.u.copy_(wl.T)
+            mix.rkl2_superstep(wl.u, ratio * dte, dte)  # warm
+            wl.u.copy_(wl.T)
+            e0.record()
+            s = mix.rkl2_superstep(wl.u, ratio * dte, dte)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            err = (torch.linalg.vector_norm(wl.u - ref) / torch.linalg.vector_norm(ref - wl.T)).item()
+            err_u = (torch.linalg.vector_norm(wl.u - ref) / torch.linalg.vector_norm(ref)).item()
+            out[f"rkl2_{int(ratio)}"] = {"s": s, "ms": ms, "cell_updates_per_s": wl.N * s / ms * 1e3,
+                                         "err_rel_change": err, "err_rel_u": err_u}
+            for pc, name in ((R.RKL_PC_JACOBI, "jacobi"), (R.RKL_PC_BILU0, "bilu0")):
+                wl.u.copy_(wl.T)
+                e0.record()
+                code, its, rel = mix.be_pcg_solve(wl.u, ratio * dte, pc=pc, block=BLOCK, rtol=RTOL, maxit=MAXIT)
+                e1.record()
+                torch.cuda.synchronize()
+                out[f"be_{name}_{int(ratio)}"] = {"fp32_iters": its[0], "relres_fp64": rel[0],
+                                                  "ms": e0.elapsed_time(e1), "converged": code == R.RKL_OK}
+    finally:
+        mix.close()
+    return out
+
+
+def variants_report(wl, torch):
+    """Sec. 6 remedies at dt = 1000 dt_exp: cost of 10 RKL2 sub-cycles and of an explicit
+    Euler prefix over a quarter of the step, next to one RKL2 super-step."""
+    dte = wl.ctx_c.set_conduction(wl.T, wl.b, wl.n)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {}
+    for name, kw in (("rkl2", {}), ("rkl2_10_cycles", {"cycles": 10}), ("euler_prefix_0.25", {"euler_fraction": 0.25}),
+                     ("rkl1_plus_2", {"scheme": 1, "extra_stages": 2})):
+        wl.u.copy_(wl.T)
+        e0.record()
+        n = wl.ctx_c.sts_advance(wl.u, 1000 * dte, dte, **kw)
+        e1.record()
+        torch.cuda.synchronize()
+        out[name] = {"operator_applications": n, "ms": e0.elapsed_time(e1)}
+    return out
+
+
 def accuracy_report(wl, torch):
     """Relative L2 error of one large step of each method against the semi-discrete
     solution exp(dt M) T, approximated by 64 RKL2 sub-steps of dt/64 (FP64 GPU path)."""
@@ -411,16 +468,17 @@ def profile_case(args):
     c = synth.conduction_case(nr, nth, nph, args.seed)
     dev = lambda a: torch.from_numpy(np.array(a, dtype=np.float64)).cuda().view(-1)  # noqa: E731
     T, b, n = dev(c["T"]), dev(c["bhat"]), dev(c["n"])
-    ctx = R.Context(c["rf"], nth, nph)
+    mixed = args.profile.endswith("-mix")
+    ctx = R.Context(c["rf"], nth, nph, prec=R.RKL_F32MIX if mixed else R.RKL_F64)
     dte = ctx.set_conduction(T, b, n)
     u = T.clone()
-    if args.profile == "stage":
+    if args.profile in ("stage", "stage-mix"):
         ctx.rkl2_superstep(u, 10 * dte, dte, s=4)
     elif args.profile == "apply":
         F = torch.empty_like(T)
         for _ in range(3):
             ctx.apply_F(T, F)
-    elif args.profile == "pcg-jacobi":
+    elif args.profile in ("pcg-jacobi", "pcg-jacobi-mix"):
         ctx.be_pcg_solve(u, 100 * dte, pc=R.RKL_PC_JACOBI, rtol=0.0, maxit=3)
     elif args.profile == "pcg-bilu0":
         ctx.be_pcg_solve(u, 100 * dte, pc=R.RKL_PC_BILU0, block=BLOCK, rtol=0.0, maxit=3)
@@ -553,6 +611,8 @@ def main():
         detail["paths"] = path_timings(wl, torch)
         if not args.no_accuracy:
             detail["accuracy_vs_semidiscrete"] = accuracy_report(wl, torch)
+            detail["mixed_precision"] = mixed_report(wl, R, torch)
+            detail["sec6_variants"] = variants_report(wl, torch)
 
     e2e = None
     if not args.no_e2e:

@@ -780,7 +780,8 @@ static int pcg_run(rkl_ctx *ctx, double *x, const double *u, const double *x0, d
 // Mixed precision: FP64 iterative refinement around FP32 PCG.  Each outer step computes
 // the FP64 residual r = W u - (W + dt S) x and its norm, stops when ||r|| <= rtol ||W u||,
 // otherwise solves (W + dt S) e = r / sigma in FP32 (sigma = RMS of r) to the relative
-// tolerance inner_rtol and updates x += sigma e in FP64.  iters counts FP32 iterations.
+// tolerance max(inner_rtol, 0.3 rtol ||b|| / ||r||) and updates x += sigma e in FP64.
+// iters counts FP32 iterations.
 template <int OP>
 static int pcg_run_mixed(rkl_ctx *ctx, double *x, const double *u, const double *x0, double dt,
                          int pc, double rtol, int maxit, int *iters, double *relres, int *status) {
@@ -834,7 +835,11 @@ static int pcg_run_mixed(rkl_ctx *ctx, double *x, const double *u, const double 
     }
     if (total >= maxit) break;
     const double sigma = std::sqrt(rn2 / (double)N);
-    if ((rc = state_upload(ctx, ctx->inner_rtol, maxit - total))) return rc;
+    // the correction only has to bring ||r|| down to the target: relative tolerance
+    // max(inner_rtol, 0.3 rtol ||b|| / ||r||), at most 0.5
+    double eta = ctx->inner_rtol;
+    if (rtol > 0.0) eta = std::min(0.5, std::max(eta, 0.3 * rtol * std::sqrt(bn2 / rn2)));
+    if ((rc = state_upload(ctx, eta, maxit - total))) return rc;
     {
       ProfScope prof(ctx, RKL_K_PCG_INIT);
       k_scale_to_f32<<<g, RB, 0, ctx->stream>>>(N, ctx->r, 1.0 / sigma, ctx->r32, ctx->e32, ctx->partials,
