@@ -441,6 +441,20 @@ def accuracy_report(wl, torch):
     return out
 
 
+def aggregate(ms: float, units: float, dist=None, device=None):
+    """Whole-job figures of independent replicas: the slowest rank's time and the sum of
+    the cell-updates of all ranks (value = units / time).  dist None = one process."""
+    if dist is None:
+        return ms, units
+    import torch
+
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return t.item(), u.item()
+
+
 def nvtx(name=None):
     """Push (name) or pop (None) an NVTX range so that an ncu launch list can be limited
     to the timed region; a no-op where NVTX is unavailable."""
@@ -553,15 +567,7 @@ def main():
     wl.ctx_c.profile_enable(False)
     wl.ctx_v.profile_enable(False)
     ms = t_start.elapsed_time(t_end)
-    if world > 1:
-        t = torch.tensor([ms, float(units)], dtype=torch.float64, device="cuda")
-        tmax = t[:1].clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        tsum = t[1:].clone()
-        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
-        ms, units_all = tmax.item(), tsum.item()
-    else:
-        units_all = float(units)
+    ms, units_all = aggregate(ms, float(units), dist if world > 1 else None, "cuda")
     value = units_all / (ms * 1e-3)
 
     # roofline of the dominant kernel: the kernel family with the largest total time in
@@ -628,12 +634,7 @@ def main():
             eu += u
         torch.cuda.synchronize()
         et = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([et, float(eu)], dtype=torch.float64, device="cuda")
-            a, b = t[:1].clone(), t[1:].clone()
-            dist.all_reduce(a, op=dist.ReduceOp.MAX)
-            dist.all_reduce(b, op=dist.ReduceOp.SUM)
-            et, eu = a.item(), b.item()
+        et, eu = aggregate(et, float(eu), dist if world > 1 else None, "cuda")
         e2e = {"value": eu / et, "unit": "cell-updates/s", "h2d_bytes_per_step": hw.h2d,
                "d2h_bytes_per_step": hw.d2h}
 

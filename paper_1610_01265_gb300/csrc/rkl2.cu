@@ -106,10 +106,10 @@ __global__ void __launch_bounds__(BLK) k_rkl2_stage_mix(Dims d, const float *__r
                                                         const float *__restrict__ M0f,
                                                         float *dout, double *u, float mu, float nu,
                                                         float mutdt, float cm0) {
-  // 3-D launch: i from the thread, (j, k) from the grid (no index division)
-  const int i = blockIdx.x * BLK + threadIdx.x;
-  if (i >= d.nr) return;
-  const int j = blockIdx.y, k = blockIdx.z;
+  // 3-D launch: i and j from a 2-D block, k from the grid (no index division)
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y, k = blockIdx.z;
+  if (i >= d.nr || j >= d.nth) return;
   const long long c = ((long long)k * d.nth + j) * d.nr + i;
   Nbr n = neighbours(d, i, j, k);
   const float f = -invW[c] * S_apply<OP, float>(d, coef, dm1, c, n);
@@ -150,12 +150,14 @@ int launch_rkl2_first_mix(rkl_ctx *ctx, const double *Y0, float *M0f, float *d1,
 int launch_rkl2_stage_mix(rkl_ctx *ctx, const float *dm1, const float *dm2, const float *M0f,
                           float *dout, double *u, double mu, double nu, double mutdt, double cm0) {
   ProfScope prof(ctx, RKL_K_RKL2_STAGE);
-  const dim3 grid(grid_for(ctx->d.nr, BLK), (unsigned)ctx->d.nth, (unsigned)ctx->d.nph);
+  // a block of 256 threads: the whole (padded) r line when it is short, several theta rows
+  const unsigned bx = (unsigned)std::min(256, ((ctx->d.nr + 31) / 32) * 32), by = 256 / bx;
+  const dim3 block(bx, by), grid(grid_for(ctx->d.nr, bx), grid_for(ctx->d.nth, by), (unsigned)ctx->d.nph);
   if (ctx->op == RKL_OP_CONDUCTION)
-    k_rkl2_stage_mix<RKL_OP_CONDUCTION><<<grid, BLK, 0, ctx->stream>>>(
+    k_rkl2_stage_mix<RKL_OP_CONDUCTION><<<grid, block, 0, ctx->stream>>>(
         ctx->d, ctx->coef32, ctx->invW32, dm1, dm2, M0f, dout, u, (float)mu, (float)nu, (float)mutdt, (float)cm0);
   else
-    k_rkl2_stage_mix<RKL_OP_VISCOSITY><<<grid, BLK, 0, ctx->stream>>>(
+    k_rkl2_stage_mix<RKL_OP_VISCOSITY><<<grid, block, 0, ctx->stream>>>(
         ctx->d, ctx->coef32, ctx->invW32, dm1, dm2, M0f, dout, u, (float)mu, (float)nu, (float)mutdt, (float)cm0);
   ctx->launches += 1;
   return cuda_check(ctx, cudaGetLastError(), "mixed rkl2 stage launch");
