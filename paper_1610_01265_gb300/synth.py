@@ -23,6 +23,9 @@ Sec. 5 and Table 1, whose ADAPT map and restart files are not available):
 * B = dipole (2 cos(t), sin(t), 0)/r^3 plus a seeded quadrupole
   -grad(x^T Q x / |x|^5) scaled to 10% of the dipole's RMS on the r = 1 shell;
   bhat = B/|B| (bhat = rhat where |B| < 1e-12 max|B|).
+* heating (a time sequence of backward-Euler steps): a source q(x, n) in K/s added
+  explicitly before each implicit step n, q = q0 h(x) (1 + 0.25 sin(2 pi n / 50 + psi))
+  with h = exp(-(r - 1)/0.3) (1 + 0.5 xi_h), psi ~ U[0, 2 pi); q0 is set by the caller.
 * viscosity case: rho = m_p 1e8 r^-4, nu = 6.7e15 (1 + 0.1 xi_nu) cm^2/s, and a
   divergence-free v = curl(xi_1, xi_2, xi_3) in Cartesian components scaled to
   max|v| = 3e7 cm/s.
@@ -192,6 +195,23 @@ def viscosity_case(nr: int, nth: int, nph: int, seed: int = 1) -> dict:
         "nu": np.array(np.broadcast_to(nu, (nph, nth, nr)), dtype=np.float64),
         "v": np.ascontiguousarray(v, dtype=np.float64),
     }
+
+
+def heating_case(nr: int, nth: int, nph: int, seed: int = 1) -> dict:
+    """Seeded heating pattern h (>= 0.5 exp(-(r-1)/0.3)) and phase psi of its modulation."""
+    rng = np.random.default_rng(seed + 2000)
+    rf = r_faces(nr)
+    r, t, p = sample_points(nr, nth, nph, rf)
+    x, y, z = _cartesian(r, t, p)
+    xi = smooth_noise(rng, x, y, z)
+    h = np.exp(-(r - 1.0) / 0.3) * (1.0 + 0.5 * xi)
+    return {"h": np.ascontiguousarray(np.broadcast_to(h, (nph, nth, nr)), dtype=np.float64),
+            "psi": float(rng.uniform(0.0, 2.0 * np.pi))}
+
+
+def heating_modulation(step: int, psi: float) -> float:
+    """Time factor of the heating source at step n."""
+    return 1.0 + 0.25 * np.sin(2.0 * np.pi * step / 50.0 + psi)
 
 
 def random_field(shape, seed: int, lo: float = -1.0, hi: float = 1.0) -> np.ndarray:
