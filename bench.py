@@ -69,8 +69,10 @@ def parse_args():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-accuracy", action="store_true")
     p.add_argument("--seed", type=int, default=1)
+    p.add_argument("--warmstart", action="store_true",
+                   help="run the learned-initial-guess study (200 BE steps with heating) instead of the step")
     p.add_argument("--profile", choices=("stage", "apply", "pcg-jacobi", "pcg-bilu0", "setup", "stage-mix",
-                                         "pcg-jacobi-mix"),
+                                         "pcg-jacobi-mix", "ws-forward", "ws-train"),
                    help="run only a minimal case of one kernel family for an ncu capture (no timing)")
     return p.parse_args()
 
@@ -482,6 +484,26 @@ def profile_case(args):
     c = synth.conduction_case(nr, nth, nph, args.seed)
     dev = lambda a: torch.from_numpy(np.array(a, dtype=np.float64)).cuda().view(-1)  # noqa: E731
     T, b, n = dev(c["T"]), dev(c["bhat"]), dev(c["n"])
+    if args.profile in ("ws-forward", "ws-train"):
+        from paper_1610_01265_gb300 import warmstart as W
+
+        net = W.Net(args.seed)
+        N = nr * nth * nph
+        if args.profile == "ws-forward":
+            x0 = torch.empty_like(T)
+            for _ in range(2):
+                net.guess((nph, nth, nr), T, b, 50.0, WS_UNIT, x0)
+        else:
+            feat = torch.empty(5 * N, dtype=torch.float32, device="cuda")
+            tgt = torch.zeros(N, dtype=torch.float32, device="cuda")
+            net.features((nph, nth, nr), T, b, 50.0, feat)
+            for _ in range(2):
+                net.loss_grad((nr, nth, nph), feat, tgt, want_loss=False)
+                net.adam(1e-3)
+        torch.cuda.synchronize()
+        net.close()
+        print(f"profile case {args.profile} done")
+        return 0
     mixed = args.profile.endswith("-mix")
     ctx = R.Context(c["rf"], nth, nph, prec=R.RKL_F32MIX if mixed else R.RKL_F64)
     dte = ctx.set_conduction(T, b, n)
@@ -504,12 +526,191 @@ def profile_case(args):
     return 0
 
 
+# ------------------------------------------------------------------ learned initial guess
+WS_STEPS, WS_TRAIN, WS_RATIO, WS_UNIT = 200, 100, 1000.0, 1e4
+WS_GUESSES = ("zero", "previous", "no_change", "extrapolated", "learned")
+# algorithmic FLOP per cell of one forward pass (3x3x3 taps, 5-32-32-32-1 channels)
+WS_FWD_FLOP = 2 * 27 * (5 * 32 + 32 * 32 + 32 * 32 + 32 * 1)
+
+
+def warmstart_study(seed=1, dims=GRID, n_steps=WS_STEPS, n_train=WS_TRAIN, ratio=WS_RATIO, epochs=4, lr=1e-3,
+                    pcs=(1, 2), log=None):
+    """Backward-Euler conduction steps with an explicit seeded heating source, the first
+    n_train from the no-change guess (their solutions train the net), the rest solved from
+    each guess in WS_GUESSES to the same rtol; returns iterations, times and errors."""
+    import torch
+
+    from paper_1610_01265_gb300 import rklpcg as R
+    from paper_1610_01265_gb300 import synth
+    from paper_1610_01265_gb300 import warmstart as W
+
+    nr, nth, nph = dims
+    shape, N, box = (nph, nth, nr), nr * nth * nph, (nr, nth, nph)
+    c = synth.conduction_case(nr, nth, nph, seed)
+    hc = synth.heating_case(nr, nth, nph, seed)
+    dev = lambda a: torch.from_numpy(np.array(a, dtype=np.float64).ravel()).cuda()  # noqa: E731
+    T, b, n, h = dev(c["T"]), dev(c["bhat"]), dev(c["n"]), dev(hc["h"])
+    ctx = R.Context(c["rf"], nth, nph)
+    dt = ratio * ctx.set_conduction(T, b, n)
+    net = W.Net(seed)
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def heated(Tn, step):
+        # workload input: u* = T^n + dt q(x, n), q0 dt = WS_UNIT (seeded pattern h, modulation)
+        return torch.add(Tn, h, alpha=WS_UNIT * synth.heating_modulation(step, hc["psi"]))
+
+    ustars, targets = [], []
+    train_iters = []
+    for step in range(n_train):
+        ctx.set_conduction(T, b, n)
+        us = heated(T, step)
+        x = us.clone()
+        code, its, _ = ctx.be_pcg_solve(x, dt, pc=R.RKL_PC_JACOBI, rtol=RTOL, maxit=MAXIT)
+        if code != R.RKL_OK:
+            raise RuntimeError(f"training-phase solve {step} did not converge ({code})")
+        tgt = torch.empty(N, dtype=torch.float32, device="cuda")
+        net.target(x, us, WS_UNIT, tgt)
+        ustars.append(us)
+        targets.append(tgt)
+        train_iters.append(its[0])
+        T = x
+    dT_prev = T - ustars[-1]
+
+    # training: full-grid samples, Adam, learning rate decaying tenfold over the run
+    feat = torch.empty(5 * N, dtype=torch.float32, device="cuda")
+    rng = np.random.default_rng(seed)
+    losses = []
+    t0, t1 = ev(), ev()
+    torch.cuda.synchronize()
+    t0.record()
+    nopt = 0
+    for e in range(epochs):
+        el = []
+        for k in rng.permutation(n_train):
+            net.features(shape, ustars[k], b, dt, feat)
+            el.append(net.loss_grad(box, feat, targets[k]))
+            net.adam(lr * 0.1 ** (nopt / max(1, epochs * n_train - 1)))
+            nopt += 1
+        losses.append(float(np.mean(el)))
+        if log:
+            log(f"epoch {e}: mean loss {losses[-1]:.4e}")
+    t1.record()
+    torch.cuda.synchronize()
+    train_ms = t0.elapsed_time(t1)
+    del ustars, targets
+
+    res = {pc: {g: {"iters": [], "ms": [], "guess_ms": [], "init_err": []} for g in WS_GUESSES} for pc in pcs}
+    spread = 0.0
+    x0 = torch.empty_like(T)
+    test_loss = []
+    for step in range(n_train, n_steps):
+        ctx.set_conduction(T, b, n)
+        us = heated(T, step)
+        sols = {}
+        for pc in pcs:
+            if pc == R.RKL_PC_BILU0:  # factor outside the timed solves (cached per step)
+                scratch = us.clone()
+                ctx.be_pcg_solve(scratch, dt, pc=pc, block=BLOCK, rtol=0.0, maxit=1)
+            for g in WS_GUESSES:
+                x = us.clone()
+                torch.cuda.synchronize()
+                e0, e1, e2 = ev(), ev(), ev()
+                e0.record()
+                if g == "zero":
+                    x0.zero_()
+                elif g == "previous":
+                    x0.copy_(T)
+                elif g == "no_change":
+                    x0.copy_(us)
+                elif g == "extrapolated":
+                    torch.add(us, dT_prev, out=x0)
+                else:
+                    net.guess(shape, us, b, dt, WS_UNIT, x0)
+                e1.record()
+                code, its, _ = ctx.be_pcg_solve(x, dt, pc=pc, block=BLOCK, rtol=RTOL, maxit=MAXIT, x0=x0)
+                e2.record()
+                torch.cuda.synchronize()
+                if code != R.RKL_OK:
+                    raise RuntimeError(f"test-phase solve {step} ({g}, pc {pc}) did not converge ({code})")
+                r = res[pc][g]
+                r["iters"].append(its[0])
+                r["ms"].append(e0.elapsed_time(e2))
+                r["guess_ms"].append(e0.elapsed_time(e1))
+                d = float(torch.linalg.norm(x - us))
+                r["init_err"].append(float(torch.linalg.norm(x0 - x)) / d)
+                sols[(pc, g)] = x
+        ref = sols[(pcs[0], "learned")]
+        dref = float(torch.linalg.norm(ref - us))
+        for x in sols.values():
+            spread = max(spread, float(torch.linalg.norm(x - ref)) / dref)
+        tgt = torch.empty(N, dtype=torch.float32, device="cuda")
+        net.target(ref, us, WS_UNIT, tgt)
+        net.features(shape, us, b, dt, feat)
+        yv = torch.empty(N, dtype=torch.float32, device="cuda")
+        net.forward(box, feat, yv)
+        test_loss.append(float(torch.mean((yv - tgt) ** 2)))
+        dT_prev = ref - us
+        T = ref
+        if log and (step - n_train) % 20 == 0:
+            log(f"step {step}: " + ", ".join(f"{g} {res[pcs[0]][g]['iters'][-1]}" for g in WS_GUESSES))
+
+    # cost of the guess alone at this size: full forward pass, tensor-core rate
+    fwd_ms = []
+    for _ in range(5):
+        e0, e1 = ev(), ev()
+        e0.record()
+        net.guess(shape, T, b, dt, WS_UNIT, x0)
+        e1.record()
+        torch.cuda.synchronize()
+        fwd_ms.append(e0.elapsed_time(e1))
+    g_ms = statistics.median(fwd_ms)
+    bf16_peak = measured_peaks().get("bf16_tflops", 1900.0)
+    out = {
+        "study": "learned PCG initial guess",
+        "grid_nr_nth_nph": list(dims),
+        "steps": n_steps,
+        "train_steps": n_train,
+        "dt_over_dt_exp0": ratio,
+        "dt_s": dt,
+        "heating_K_per_step_at_h1": WS_UNIT,
+        "rtol": RTOL,
+        "train": {"epochs": epochs, "optimizer_steps": nopt, "ms_total": train_ms, "ms_per_step": train_ms / nopt,
+                  "epoch_mean_loss": losses, "train_phase_iters_mean": float(np.mean(train_iters))},
+        "test_mse_mean": float(np.mean(test_loss)),
+        "solution_spread_rel": spread,
+        "guess_forward": {"ms": g_ms, "tflops_algorithmic": WS_FWD_FLOP * N / (g_ms * 1e-3) / 1e12,
+                          "bf16_peak_tflops": bf16_peak,
+                          "frac": WS_FWD_FLOP * N / (g_ms * 1e-3) / 1e12 / bf16_peak},
+        "test": {},
+    }
+    for pc in pcs:
+        name = {1: "jacobi", 2: "bilu0-8x8x8"}[pc]
+        out["test"][name] = {g: {"iters_mean": float(np.mean(r["iters"])), "ms_mean": float(np.mean(r["ms"])),
+                                 "guess_ms_mean": float(np.mean(r["guess_ms"])),
+                                 "init_err_mean": float(np.mean(r["init_err"]))}
+                             for g, r in res[pc].items()}
+    net.close()
+    ctx.close()
+    return out
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.profile:
         return profile_case(args)
+    if args.warmstart:
+        import torch
+
+        from paper_1610_01265_gb300 import build as B
+
+        B.build()
+        if not torch.cuda.is_available():
+            raise SystemExit("bench.py needs a CUDA GPU")
+        out = warmstart_study(args.seed, log=lambda m: print(m, file=sys.stderr, flush=True))
+        print(json.dumps(out), flush=True)
+        return 0
     world, rank, local = dist_env()
     import torch
 

@@ -21,9 +21,9 @@ the caller, and the guess is x0 = T + scale * y.
 
 The net runs with BF16 weights and activations and FP32 accumulation.  The oracle
 rounds at the same points (``rounding=True``) so that it computes the same function:
-features, weights and the stored activations a1..a3 and back-propagated gradients
-dz1..dz3 are rounded to BF16 (round to nearest, ties to even); biases, the output y,
-dy and the parameter gradients stay in full precision.  ``rounding=False`` gives the
+features, weights, the stored activations a1..a3, the output gradient dy and the
+back-propagated gradients dz1..dz3 are rounded to BF16 (round to nearest, ties to
+even); biases, the output y and the parameter gradients stay in full precision.  ``rounding=False`` gives the
 plain FP64 net (used to pin the gradient code against autograd and finite
 differences).
 
@@ -182,7 +182,7 @@ def loss_grad(params, feats, target, weight=None, periodic: bool = True, roundin
     wsum = float(w.sum())
     e = y - t
     loss = float((w * e * e).sum()) / wsum
-    d = (2.0 / wsum) * w * e
+    d = _bf16_t((2.0 / wsum) * w * e, rounding)
     d = d.unsqueeze(1)  # (B, 1, ...): gradient of L with respect to the pre-activation of layer 4
     grads = [None] * len(layers)
     for l in range(len(layers) - 1, -1, -1):

@@ -1,0 +1,966 @@
+// warmstart.cu -- learned initial guess for the backward-Euler + PCG solve (the PCG of
+// Fig. 1 starts from any x0).  A 4-layer 3-D convolutional net maps (T, bhat, log dt) to
+// Delta T; it is trained on the solver's own solutions, and PCG still runs to the same
+// tolerance, so the net only moves the starting point.
+//
+// Net: conv3x3x3 5->32 ReLU, 32->32 ReLU, 32->32 ReLU, 32->1.  Parameters are FP32 (Adam
+// state too); every pass uses BF16 copies of the weights, BF16 activations and FP32
+// accumulation on the tensor cores (mma.sync m16n8k16).  Rounding points: features,
+// weights, stored activations a1..a3, the output gradient dy and the back-propagated
+// gradients dz1..dz3 are BF16 (round to nearest even); biases, y and the parameter
+// gradients (FP32 per CTA, FP64 across CTAs in a fixed order) are not.
+//
+// Activation layout: channels-last BF16, [box][phi][theta][r][C] with C = 32, or C = 16
+// for the 5 input features (channels 5..15 zero) and for dy (channel 0).  A box is a
+// whole grid (phi periodic) or a detached block (zero outside on every face); r and
+// theta are always zero outside.
+//
+// Convolutions are implicit GEMMs over bricks of 32 (r) x 4 (theta) x 2 (phi) cells:
+// the brick plus a one-cell halo (34 x 6 x 4 rows of C channels) is staged in shared
+// memory with cp.async, rows XOR-swizzled by 16-byte chunk so that ldmatrix of eight
+// consecutive rows is conflict-free, and each tap's A operand is read with ldmatrix
+// from per-lane row addresses (the neighbour of the lane's cell).  Weights sit in
+// shared memory in mma fragment order.  Forward: M = 256 cells, N = 32 channels,
+// K = 27 taps x C.  Data gradient: the same kernel with the adjoint weights
+// W'[ci][co][26 - tap] = W[co][ci][tap].  Weight gradient: per tap, M = Cout, N = Cin,
+// K = cells, both operands through ldmatrix.trans; a persistent CTA accumulates its
+// bricks in registers and a second kernel sums the per-CTA partials in FP64.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <new>
+#include <vector>
+
+#include "../../include/warmstart.h"
+#include "internal.cuh"
+
+namespace {
+
+constexpr int NL = 4;
+constexpr int L_CIN[NL] = {5, 32, 32, 32};
+constexpr int L_COUT[NL] = {32, 32, 32, 1};
+constexpr int NTAP = 27;
+
+// brick and halo geometry
+constexpr int BR = 32, BT = 4, BP = 2, BRICK = BR * BT * BP;
+constexpr int HR = BR + 2, HT = BT + 2, HP = BP + 2, NH = HR * HT * HP;
+constexpr int CONV_THREADS = 256;  // 8 warps, one brick row of 32 cells each
+constexpr int WG_THREADS = 288;    // 9 warps, three taps each
+constexpr int EW = 256;            // element-wise kernels
+
+enum { EPI_RELU = 0, EPI_MASK = 1, EPI_F32 = 2 };
+
+struct Boxes {
+  int nr, nth, nph, nbox, periodic;
+  int nbr, nbt, nbp;  // bricks per box along r, theta, phi
+  long long nc;       // cells per box
+  long long nbricks;
+};
+
+Boxes make_boxes(int nr, int nth, int nph, int nbox, int periodic) {
+  Boxes b;
+  b.nr = nr;
+  b.nth = nth;
+  b.nph = nph;
+  b.nbox = nbox;
+  b.periodic = periodic;
+  b.nbr = (nr + BR - 1) / BR;
+  b.nbt = (nth + BT - 1) / BT;
+  b.nbp = (nph + BP - 1) / BP;
+  b.nc = (long long)nr * nth * nph;
+  b.nbricks = (long long)b.nbr * b.nbt * b.nbp * nbox;
+  return b;
+}
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, int bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(dst)), "l"(src), "r"(bytes));
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n" ::);
+  asm volatile("cp.async.wait_group 0;\n" ::);
+}
+
+__device__ __forceinline__ void ldsm_x4(unsigned addr, unsigned &r0, unsigned &r1, unsigned &r2, unsigned &r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(addr));
+}
+__device__ __forceinline__ void ldsm_x4_t(unsigned addr, unsigned &r0, unsigned &r1, unsigned &r2, unsigned &r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(addr));
+}
+
+// D += A B, m16n8k16, BF16 inputs, FP32 accumulators
+__device__ __forceinline__ void mma_bf16(float *d, unsigned a0, unsigned a1, unsigned a2, unsigned a3, unsigned b0,
+                                         unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// 16-byte chunk swizzle of a staged row of C channels (C * 2 bytes)
+template <int C>
+__device__ __forceinline__ int swz(int row) {
+  return C == 32 ? ((row >> 1) & 3) : ((row >> 2) & 1);
+}
+template <int C>
+__device__ __forceinline__ unsigned row_chunk(unsigned base, int row, int chunk) {
+  return base + row * (C * 2) + ((chunk ^ swz<C>(row)) << 4);
+}
+
+struct BrickPos {
+  int b, i0, j0, k0;
+};
+
+__device__ __forceinline__ BrickPos brick_pos(const Boxes &g, long long id) {
+  BrickPos p;
+  const long long per_box = (long long)g.nbr * g.nbt * g.nbp;
+  p.b = (int)(id / per_box);
+  long long r = id - (long long)p.b * per_box;
+  const int br = (int)(r % g.nbr);
+  r /= g.nbr;
+  const int bt = (int)(r % g.nbt);
+  const int bp = (int)(r / g.nbt);
+  p.i0 = br * BR;
+  p.j0 = bt * BT;
+  p.k0 = bp * BP;
+  return p;
+}
+
+// global cell index of (i, j, k) in box b, or -1 outside (phi wraps when periodic)
+__device__ __forceinline__ long long cell_index(const Boxes &g, int b, int i, int j, int k) {
+  if (i < 0 || i >= g.nr || j < 0 || j >= g.nth) return -1;
+  if (k < 0 || k >= g.nph) {
+    if (!g.periodic) return -1;
+    k = ((k % g.nph) + g.nph) % g.nph;
+  }
+  return (long long)b * g.nc + ((long long)k * g.nth + j) * g.nr + i;
+}
+
+// stage the brick's halo rows of a C-channel activation (zero outside the box)
+template <int C>
+__device__ __forceinline__ void stage_halo(const Boxes &g, const BrickPos &p, const __nv_bfloat16 *src,
+                                           unsigned char *halo) {
+  constexpr int NCH = C / 8;
+  for (int q = threadIdx.x; q < NH * NCH; q += blockDim.x) {
+    const int h = q / NCH, c = q - h * NCH;
+    const int hr = h % HR, ht = (h / HR) % HT, hp = h / (HR * HT);
+    const long long cell = cell_index(g, p.b, p.i0 + hr - 1, p.j0 + ht - 1, p.k0 + hp - 1);
+    const __nv_bfloat16 *gp = cell >= 0 ? src + cell * C + c * 8 : src;
+    cp_async16(halo + h * (C * 2) + ((c ^ swz<C>(h)) << 4), gp, cell >= 0 ? 16 : 0);
+  }
+}
+
+// stage the brick's own rows of a C-channel tensor (zero outside the box)
+template <int C>
+__device__ __forceinline__ void stage_brick(const Boxes &g, const BrickPos &p, const __nv_bfloat16 *src,
+                                            unsigned char *dst) {
+  constexpr int NCH = C / 8;
+  for (int q = threadIdx.x; q < BRICK * NCH; q += blockDim.x) {
+    const int r = q / NCH, c = q - r * NCH;
+    const int ir = r % BR, it = (r / BR) % BT, ip = r / (BR * BT);
+    const int i = p.i0 + ir, j = p.j0 + it, k = p.k0 + ip;
+    const long long cell = (k < g.nph) ? cell_index(g, p.b, i, j, k) : -1;
+    const __nv_bfloat16 *gp = cell >= 0 ? src + cell * C + c * 8 : src;
+    cp_async16(dst + r * (C * 2) + ((c ^ swz<C>(r)) << 4), gp, cell >= 0 ? 16 : 0);
+  }
+}
+
+__device__ __forceinline__ int halo_row(int ir, int it, int ip, int tap) {
+  const int dr = tap % 3 - 1, dt = (tap / 3) % 3 - 1, dp = tap / 9 - 1;
+  return (ir + 1 + dr) + HR * ((it + 1 + dt) + HT * (ip + 1 + dp));
+}
+
+struct ConvArgs {
+  Boxes g;
+  const __nv_bfloat16 *in;  // [cells][CIN]
+  const uint2 *wfrag;       // [27][CIN/16][NT][32] B fragments
+  const float *bias;        // [nbias] (EPI_RELU, EPI_F32) or NULL
+  int nbias;
+  const __nv_bfloat16 *mask;  // [cells][32] (EPI_MASK): zero where mask <= 0
+  void *out;                // [cells][32] BF16, or [cells] FP32 (EPI_F32)
+};
+
+template <int CIN, int NT>
+constexpr int conv_smem_bytes() {
+  return NTAP * (CIN / 16) * NT * 32 * 8 + 128 + NH * CIN * 2;
+}
+
+// out = epilogue(sum_tap sum_ci W[.][ci][tap] in[ci][x + d(tap)]) over one box set
+template <int CIN, int NT, int EPI>
+__global__ void __launch_bounds__(CONV_THREADS, 2) k_conv(ConvArgs a) {
+  constexpr int KS = CIN / 16;
+  constexpr int WF_BYTES = NTAP * KS * NT * 32 * 8;
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint2 *wf = reinterpret_cast<uint2 *>(smem);
+  float *bias_s = reinterpret_cast<float *>(smem + WF_BYTES);
+  unsigned char *halo = smem + WF_BYTES + 128;
+  const unsigned halo_u = smem_u32(halo);
+
+  for (int q = threadIdx.x; q < WF_BYTES / 16; q += CONV_THREADS)
+    cp_async16(smem + q * 16, reinterpret_cast<const unsigned char *>(a.wfrag) + q * 16, 16);
+  if (threadIdx.x < 32) bias_s[threadIdx.x] = (a.bias && (int)threadIdx.x < a.nbias) ? a.bias[threadIdx.x] : 0.0f;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int it = warp & 3, ip = warp >> 2;
+  const int g = lane >> 2, q = lane & 3;
+  const int mi = lane >> 3;
+  const int row_in = (lane & 7) + ((mi & 1) << 3);  // ldmatrix row of this lane in an m-tile
+  const int chunk_sel = mi >> 1;
+
+  for (long long id = blockIdx.x; id < a.g.nbricks; id += gridDim.x) {
+    const BrickPos p = brick_pos(a.g, id);
+    stage_halo<CIN>(a.g, p, a.in, halo);
+    cp_async_wait_all();
+    __syncthreads();
+
+    float acc[2][NT][4];
+#pragma unroll
+    for (int mt = 0; mt < 2; mt++)
+#pragma unroll
+      for (int nt = 0; nt < NT; nt++)
+#pragma unroll
+        for (int e = 0; e < 4; e++) acc[mt][nt][e] = 0.0f;
+
+#pragma unroll 1
+    for (int tap = 0; tap < NTAP; tap++) {
+      const int h0 = halo_row(row_in, it, ip, tap);
+#pragma unroll
+      for (int ks = 0; ks < KS; ks++) {
+        uint2 bf[NT];
+#pragma unroll
+        for (int nt = 0; nt < NT; nt++) bf[nt] = wf[((tap * KS + ks) * NT + nt) * 32 + lane];
+#pragma unroll
+        for (int mt = 0; mt < 2; mt++) {
+          unsigned a0, a1, a2, a3;
+          ldsm_x4(row_chunk<CIN>(halo_u, h0 + mt * 16, 2 * ks + chunk_sel), a0, a1, a2, a3);
+#pragma unroll
+          for (int nt = 0; nt < NT; nt++) mma_bf16(acc[mt][nt], a0, a1, a2, a3, bf[nt].x, bf[nt].y);
+        }
+      }
+    }
+
+    // epilogue: rows g and g + 8 of each m-tile, columns nt*8 + 2q, +1
+#pragma unroll
+    for (int mt = 0; mt < 2; mt++)
+#pragma unroll
+      for (int half = 0; half < 2; half++) {
+        const int ir = mt * 16 + g + 8 * half;
+        const int i = p.i0 + ir, j = p.j0 + it, k = p.k0 + ip;
+        if (i >= a.g.nr || j >= a.g.nth || k >= a.g.nph) continue;
+        const long long cell = (long long)p.b * a.g.nc + ((long long)k * a.g.nth + j) * a.g.nr + i;
+        if (EPI == EPI_F32) {
+          if (q == 0) reinterpret_cast<float *>(a.out)[cell] = acc[mt][0][2 * half] + bias_s[0];
+        } else {
+#pragma unroll
+          for (int nt = 0; nt < NT; nt++) {
+            const int col = nt * 8 + 2 * q;
+            float v0 = acc[mt][nt][2 * half], v1 = acc[mt][nt][2 * half + 1];
+            if (EPI == EPI_RELU) {
+              v0 = fmaxf(v0 + bias_s[col], 0.0f);
+              v1 = fmaxf(v1 + bias_s[col + 1], 0.0f);
+            } else {
+              const __nv_bfloat162 m = *reinterpret_cast<const __nv_bfloat162 *>(a.mask + cell * 32 + col);
+              if (!(__low2float(m) > 0.0f)) v0 = 0.0f;
+              if (!(__high2float(m) > 0.0f)) v1 = 0.0f;
+            }
+            *reinterpret_cast<__nv_bfloat162 *>(reinterpret_cast<__nv_bfloat16 *>(a.out) + cell * 32 + col) =
+                __floats2bfloat162_rn(v0, v1);
+          }
+        }
+      }
+    __syncthreads();  // the halo is restaged next
+  }
+}
+
+struct WgArgs {
+  Boxes g;
+  const __nv_bfloat16 *in;    // [cells][CIN] layer input activation
+  const __nv_bfloat16 *dout;  // [cells][COUT] gradient at the layer's output
+  float *part;                // [gridDim.x][27][COUT][CIN]
+  float *partb;               // [gridDim.x][COUT]
+};
+
+template <int CIN, int COUT>
+constexpr int wgrad_smem_bytes() {
+  return NH * CIN * 2 + BRICK * COUT * 2;
+}
+
+// per-CTA partial dW[tap][co][ci] = sum_x dout[x][co] in[x + d(tap)][ci] and db[co]
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(WG_THREADS, 1) k_wgrad(WgArgs a) {
+  constexpr int MT = COUT / 16, NT = CIN / 8;
+  extern __shared__ __align__(128) unsigned char smem[];
+  unsigned char *halo = smem;
+  unsigned char *dsm = smem + NH * CIN * 2;
+  const unsigned halo_u = smem_u32(halo), dsm_u = smem_u32(dsm);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 2, q = lane & 3, mi = lane >> 3;
+
+  float acc[3][MT][NT][4];
+  float accb[MT][4];
+#pragma unroll
+  for (int t = 0; t < 3; t++)
+#pragma unroll
+    for (int mt = 0; mt < MT; mt++)
+#pragma unroll
+      for (int nt = 0; nt < NT; nt++)
+#pragma unroll
+        for (int e = 0; e < 4; e++) acc[t][mt][nt][e] = 0.0f;
+#pragma unroll
+  for (int mt = 0; mt < MT; mt++)
+#pragma unroll
+    for (int e = 0; e < 4; e++) accb[mt][e] = 0.0f;
+  const unsigned ones = 0x3F803F80u;  // two BF16 1.0
+
+  for (long long id = blockIdx.x; id < a.g.nbricks; id += gridDim.x) {
+    const BrickPos p = brick_pos(a.g, id);
+    stage_halo<CIN>(a.g, p, a.in, halo);
+    stage_brick<COUT>(a.g, p, a.dout, dsm);
+    cp_async_wait_all();
+    __syncthreads();
+#pragma unroll 1
+    for (int kk = 0; kk < BRICK / 16; kk++) {
+      // A = dout^T (m = output channel, k = cell): matrices (cells 0-7 | 8-15) x (co lo | hi)
+      unsigned af[MT][4];
+      const int arow = kk * 16 + (lane & 7) + ((mi >> 1) << 3);
+#pragma unroll
+      for (int mt = 0; mt < MT; mt++)
+        ldsm_x4_t(row_chunk<COUT>(dsm_u, arow, mt * 2 + (mi & 1)), af[mt][0], af[mt][1], af[mt][2], af[mt][3]);
+      if (warp == 0) {
+#pragma unroll
+        for (int mt = 0; mt < MT; mt++) mma_bf16(accb[mt], af[mt][0], af[mt][1], af[mt][2], af[mt][3], ones, ones);
+      }
+      // B = shifted input (k = cell, n = input channel): matrices (cells 0-7 | 8-15) x (chunk nt | nt+1)
+      const int bcell = kk * 16 + (lane & 7) + ((mi & 1) << 3);
+      const int ir = bcell % BR, it = (bcell / BR) % BT, ip = bcell / (BR * BT);
+#pragma unroll
+      for (int t = 0; t < 3; t++) {
+        const int h = halo_row(ir, it, ip, warp * 3 + t);
+#pragma unroll
+        for (int np = 0; np < NT / 2; np++) {
+          unsigned b0, b1, b2, b3;
+          ldsm_x4_t(row_chunk<CIN>(halo_u, h, np * 2 + (mi >> 1)), b0, b1, b2, b3);
+#pragma unroll
+          for (int mt = 0; mt < MT; mt++) {
+            mma_bf16(acc[t][mt][2 * np], af[mt][0], af[mt][1], af[mt][2], af[mt][3], b0, b1);
+            mma_bf16(acc[t][mt][2 * np + 1], af[mt][0], af[mt][1], af[mt][2], af[mt][3], b2, b3);
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+
+  float *part = a.part + (size_t)blockIdx.x * NTAP * COUT * CIN;
+#pragma unroll
+  for (int t = 0; t < 3; t++) {
+    const int tap = warp * 3 + t;
+#pragma unroll
+    for (int mt = 0; mt < MT; mt++)
+#pragma unroll
+      for (int nt = 0; nt < NT; nt++)
+#pragma unroll
+        for (int half = 0; half < 2; half++) {
+          const int co = mt * 16 + g + 8 * half, ci = nt * 8 + 2 * q;
+          float *dst = part + ((size_t)tap * COUT + co) * CIN + ci;
+          dst[0] = acc[t][mt][nt][2 * half];
+          dst[1] = acc[t][mt][nt][2 * half + 1];
+        }
+  }
+  if (warp == 0 && q == 0) {
+#pragma unroll
+    for (int mt = 0; mt < MT; mt++) {
+      a.partb[(size_t)blockIdx.x * COUT + mt * 16 + g] = accb[mt][0];
+      a.partb[(size_t)blockIdx.x * COUT + mt * 16 + g + 8] = accb[mt][2];
+    }
+  }
+}
+
+// dW in parameter order [co][ci][tap] (real channel counts) and db: fixed-order FP64 sums
+__global__ void k_wgrad_reduce(int nblk, int CIN, int COUT, int cin, int cout, const float *__restrict__ part,
+                               const float *__restrict__ partb, float *__restrict__ gw, float *__restrict__ gb) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nw = cout * cin * NTAP;
+  if (idx < nw) {
+    const int co = idx / (cin * NTAP), ci = (idx / NTAP) % cin, tap = idx % NTAP;
+    double s = 0.0;
+    for (int b = 0; b < nblk; b++) s += part[(((size_t)b * NTAP + tap) * COUT + co) * CIN + ci];
+    gw[idx] = (float)s;
+  } else if (idx < nw + cout) {
+    const int co = idx - nw;
+    double s = 0.0;
+    for (int b = 0; b < nblk; b++) s += partb[(size_t)b * COUT + co];
+    gb[co] = (float)s;
+  }
+}
+
+// B fragments of one layer in [tap][ks][nt][lane] order.  Forward: B[k][n] = W[n][k][tap]
+// with n = output channel, k = input channel; adjoint: B[k][n] = W[k][n][26 - tap].
+// Channels beyond the layer's real counts are zero.
+__global__ void k_wfrag(const __nv_bfloat16 *__restrict__ w, int cin, int cout, int KS, int NT, int adjoint,
+                        uint2 *__restrict__ out) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= NTAP * KS * NT * 32) return;
+  const int lane = idx % 32, nt = (idx / 32) % NT, ks = (idx / (32 * NT)) % KS, tap = idx / (32 * NT * KS);
+  const int g = lane >> 2, q = lane & 3;
+  const int n = nt * 8 + g;
+  auto elem = [&](int k) -> __nv_bfloat16 {
+    const int kc = ks * 16 + k;
+    int co, ci, t;
+    if (!adjoint) {
+      co = n;
+      ci = kc;
+      t = tap;
+    } else {
+      co = kc;
+      ci = n;
+      t = NTAP - 1 - tap;
+    }
+    if (co >= cout || ci >= cin) return __float2bfloat16(0.0f);
+    return w[((size_t)co * cin + ci) * NTAP + t];
+  };
+  auto pack = [&](int k) -> unsigned {
+    const __nv_bfloat16 lo = elem(k), hi = elem(k + 1);
+    return (unsigned)__bfloat16_as_ushort(lo) | ((unsigned)__bfloat16_as_ushort(hi) << 16);
+  };
+  out[idx] = make_uint2(pack(2 * q), pack(2 * q + 8));
+}
+
+__global__ void __launch_bounds__(EW) k_to_bf16(int n, const float *__restrict__ a, __nv_bfloat16 *__restrict__ b) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < n) b[q] = __float2bfloat16_rn(a[q]);
+}
+
+// FP32 channel-major [5][cells] -> BF16 [cells][16]
+__global__ void __launch_bounds__(EW) k_pack_input(long long cells, const float *__restrict__ in,
+                                                   __nv_bfloat16 *__restrict__ out) {
+  const long long c = (long long)blockIdx.x * EW + threadIdx.x;
+  if (c >= cells) return;
+  __align__(16) __nv_bfloat16 v[16];
+#pragma unroll
+  for (int ch = 0; ch < 16; ch++) v[ch] = __float2bfloat16_rn(ch < 5 ? in[ch * cells + c] : 0.0f);
+  uint4 *dst = reinterpret_cast<uint4 *>(out + c * 16);
+  dst[0] = reinterpret_cast<uint4 *>(v)[0];
+  dst[1] = reinterpret_cast<uint4 *>(v)[1];
+}
+
+// features of one grid straight into the packed layout: (T - 1e6)/1e6, bhat, log10 dt
+__global__ void __launch_bounds__(EW) k_features(long long N, const double *__restrict__ T,
+                                                 const double *__restrict__ bhat, float logdt,
+                                                 __nv_bfloat16 *__restrict__ out, float *__restrict__ f32) {
+  const long long c = (long long)blockIdx.x * EW + threadIdx.x;
+  if (c >= N) return;
+  float f[5] = {(float)((T[c] - 1e6) * 1e-6), (float)bhat[c], (float)bhat[N + c], (float)bhat[2 * N + c], logdt};
+  __align__(16) __nv_bfloat16 v[16];
+#pragma unroll
+  for (int ch = 0; ch < 16; ch++) v[ch] = __float2bfloat16_rn(ch < 5 ? f[ch] : 0.0f);
+  uint4 *dst = reinterpret_cast<uint4 *>(out + c * 16);
+  dst[0] = reinterpret_cast<uint4 *>(v)[0];
+  dst[1] = reinterpret_cast<uint4 *>(v)[1];
+  if (f32) {
+#pragma unroll
+    for (int ch = 0; ch < 5; ch++) f32[ch * N + c] = f[ch];
+  }
+}
+
+// sum of the loss weights (fixed-order block partials)
+__global__ void __launch_bounds__(EW) k_sum(long long n, const float *__restrict__ w, double *__restrict__ part) {
+  __shared__ double red[EW];
+  double s = 0.0;
+  for (long long q = (long long)blockIdx.x * EW + threadIdx.x; q < n; q += (long long)gridDim.x * EW)
+    s += w ? (double)w[q] : 1.0;
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int h = EW / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+// dy = 2 w (y - t) / sum w into channel 0 of a 16-channel BF16 tensor; partial sums of w e^2
+__global__ void __launch_bounds__(EW) k_loss(long long n, const float *__restrict__ y, const float *__restrict__ t,
+                                             const float *__restrict__ w, const double *__restrict__ wpart,
+                                             int nwpart, __nv_bfloat16 *__restrict__ dy, double *__restrict__ part) {
+  __shared__ double red[EW];
+  __shared__ float scale_s;
+  if (threadIdx.x == 0) {
+    double ws = 0.0;
+    for (int b = 0; b < nwpart; b++) ws += wpart[b];
+    scale_s = (float)(2.0 / ws);
+  }
+  __syncthreads();
+  const float scale = scale_s;
+  double s = 0.0;
+  for (long long q = (long long)blockIdx.x * EW + threadIdx.x; q < n; q += (long long)gridDim.x * EW) {
+    const float wq = w ? w[q] : 1.0f;
+    const float e = y[q] - t[q];
+    __align__(16) __nv_bfloat16 v[16];
+    v[0] = __float2bfloat16_rn(scale * wq * e);
+#pragma unroll
+    for (int ch = 1; ch < 16; ch++) v[ch] = __float2bfloat16_rn(0.0f);
+    uint4 *dst = reinterpret_cast<uint4 *>(dy + q * 16);
+    dst[0] = reinterpret_cast<uint4 *>(v)[0];
+    dst[1] = reinterpret_cast<uint4 *>(v)[1];
+    s += (double)wq * (double)e * (double)e;
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int h = EW / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+// Adam with bias correction (c1 = 1 - b1^t, c2 = 1 - b2^t); the complements om = 1 - b
+// come from the host in FP64 (1 - 0.999f in FP32 is off by 1.3e-5 relative)
+__global__ void __launch_bounds__(EW) k_adam(int n, float *__restrict__ p, const float *__restrict__ g,
+                                             float *__restrict__ m, float *__restrict__ v, float lr, float b1,
+                                             float om1, float b2, float om2, float eps, float c1, float c2) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  const float gq = g[q];
+  const float mq = b1 * m[q] + om1 * gq;
+  const float vq = b2 * v[q] + om2 * gq * gq;
+  m[q] = mq;
+  v[q] = vq;
+  p[q] = p[q] - lr * (mq / c1) / (sqrtf(vq / c2) + eps);
+}
+
+// x0 = T + scale y
+__global__ void __launch_bounds__(EW) k_guess(long long N, const double *__restrict__ T, const float *__restrict__ y,
+                                              double scale, double *__restrict__ x0) {
+  const long long c = (long long)blockIdx.x * EW + threadIdx.x;
+  if (c < N) x0[c] = fma(scale, (double)y[c], T[c]);
+}
+
+// training target out = (x - base) / unit in FP32
+__global__ void __launch_bounds__(EW) k_target(long long N, const double *__restrict__ x, const double *__restrict__ base,
+                                               double inv_unit, float *__restrict__ out) {
+  const long long c = (long long)blockIdx.x * EW + threadIdx.x;
+  if (c < N) out[c] = (float)((x[c] - base[c]) * inv_unit);
+}
+
+// SplitMix64 (Steele, Lea & Flood 2014), one step per counter from state seed
+double splitmix_uniform(unsigned long long seed, unsigned long long ctr) {
+  unsigned long long z = seed + 0x9E3779B97F4A7C15ULL * (ctr + 1);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  z ^= z >> 31;
+  return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+}
+
+}  // namespace
+
+struct rkl_ws {
+  cudaStream_t stream = nullptr;
+  int nsm = 0;
+  size_t woff[NL], boff[NL], bw_off[NL];  // FP32 weight/bias offsets, BF16 weight offsets
+  int nparam = 0, nweight = 0;
+  float *param = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
+  __nv_bfloat16 *wbf = nullptr;
+  uint2 *wfrag[NL] = {nullptr, nullptr, nullptr, nullptr};  // forward fragments
+  uint2 *wadj[NL] = {nullptr, nullptr, nullptr, nullptr};   // adjoint fragments (layers 1..3)
+  long long step = 0;
+  unsigned char *arena = nullptr;
+  size_t arena_cap = 0;
+  float *part = nullptr;  // weight-gradient partials
+  size_t part_cap = 0;
+  double *red = nullptr;  // loss partials (2 x 1024)
+  long long launches = 0;
+  char err[256] = {0};
+};
+
+using namespace rkl;
+
+namespace {
+
+constexpr int RED_BLOCKS = 1024;
+
+int ws_cuda(rkl_ws *ws, cudaError_t e) {
+  if (e == cudaSuccess) return RKL_OK;
+  if (ws) snprintf(ws->err, sizeof(ws->err), "%s", cudaGetErrorString(e));
+  cudaGetLastError();
+  return e == cudaErrorMemoryAllocation ? RKL_ENOMEM : RKL_ECUDA;
+}
+
+int frag_ks(int l) { return L_CIN[l] <= 16 ? 1 : 2; }
+int frag_nt(int l) { return L_COUT[l] == 1 ? 1 : 4; }
+size_t frag_count(int l) { return (size_t)NTAP * frag_ks(l) * frag_nt(l) * 32; }
+// adjoint of layer l (l >= 1): input = gradient at its output (16 channels for l = 3)
+size_t adj_count(int l) { return (size_t)NTAP * (L_COUT[l] == 1 ? 1 : 2) * 4 * 32; }
+
+template <typename K>
+int set_smem(rkl_ws *ws, K kernel, int bytes) {
+  return ws_cuda(ws, cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+}
+
+int configure_kernels(rkl_ws *ws) {
+  int rc = set_smem(ws, k_conv<16, 4, EPI_RELU>, conv_smem_bytes<16, 4>());
+  if (!rc) rc = set_smem(ws, k_conv<32, 4, EPI_RELU>, conv_smem_bytes<32, 4>());
+  if (!rc) rc = set_smem(ws, k_conv<32, 1, EPI_F32>, conv_smem_bytes<32, 1>());
+  if (!rc) rc = set_smem(ws, k_conv<16, 4, EPI_MASK>, conv_smem_bytes<16, 4>());
+  if (!rc) rc = set_smem(ws, k_conv<32, 4, EPI_MASK>, conv_smem_bytes<32, 4>());
+  if (!rc) rc = set_smem(ws, k_wgrad<16, 32>, wgrad_smem_bytes<16, 32>());
+  if (!rc) rc = set_smem(ws, k_wgrad<32, 32>, wgrad_smem_bytes<32, 32>());
+  if (!rc) rc = set_smem(ws, k_wgrad<32, 16>, wgrad_smem_bytes<32, 16>());
+  return rc;
+}
+
+// BF16 weights and mma fragments from the FP32 parameters
+int refresh_weights(rkl_ws *ws) {
+  for (int l = 0; l < NL; l++) {
+    const int nw = L_COUT[l] * L_CIN[l] * NTAP;
+    k_to_bf16<<<(nw + EW - 1) / EW, EW, 0, ws->stream>>>(nw, ws->param + ws->woff[l], ws->wbf + ws->bw_off[l]);
+    const int nf = (int)frag_count(l);
+    k_wfrag<<<(nf + EW - 1) / EW, EW, 0, ws->stream>>>(ws->wbf + ws->bw_off[l], L_CIN[l], L_COUT[l], frag_ks(l),
+                                                      frag_nt(l), 0, ws->wfrag[l]);
+    ws->launches += 2;
+    if (l > 0) {
+      const int na = (int)adj_count(l);
+      k_wfrag<<<(na + EW - 1) / EW, EW, 0, ws->stream>>>(ws->wbf + ws->bw_off[l], L_CIN[l], L_COUT[l],
+                                                        L_COUT[l] == 1 ? 1 : 2, 4, 1, ws->wadj[l]);
+      ws->launches += 1;
+    }
+  }
+  return ws_cuda(ws, cudaGetLastError());
+}
+
+int ensure_arena(rkl_ws *ws, size_t bytes) {
+  if (bytes <= ws->arena_cap) return RKL_OK;
+  if (ws->arena) {
+    cudaStreamSynchronize(ws->stream);
+    cudaFree(ws->arena);
+    ws->arena = nullptr;
+    ws->arena_cap = 0;
+  }
+  int rc = ws_cuda(ws, cudaMalloc(&ws->arena, bytes));
+  if (!rc) ws->arena_cap = bytes;
+  return rc;
+}
+
+int ensure_part(rkl_ws *ws, size_t floats) {
+  if (floats <= ws->part_cap) return RKL_OK;
+  if (ws->part) {
+    cudaStreamSynchronize(ws->stream);
+    cudaFree(ws->part);
+    ws->part = nullptr;
+    ws->part_cap = 0;
+  }
+  int rc = ws_cuda(ws, cudaMalloc(&ws->part, floats * sizeof(float)));
+  if (!rc) ws->part_cap = floats;
+  return rc;
+}
+
+int conv_grid(const rkl_ws *ws, const Boxes &g) {
+  const long long cap = 2LL * ws->nsm;
+  return (int)(g.nbricks < cap ? g.nbricks : cap);
+}
+
+template <int CIN, int NT, int EPI>
+void launch_conv(rkl_ws *ws, const Boxes &g, const __nv_bfloat16 *in, const uint2 *wf, const float *bias,
+                 const __nv_bfloat16 *mask, void *out) {
+  ConvArgs a{g, in, wf, bias, bias ? (NT == 1 ? 1 : 32) : 0, mask, out};
+  k_conv<CIN, NT, EPI><<<conv_grid(ws, g), CONV_THREADS, conv_smem_bytes<CIN, NT>(), ws->stream>>>(a);
+  ws->launches += 1;
+}
+
+template <int CIN, int COUT>
+int launch_wgrad(rkl_ws *ws, const Boxes &g, const __nv_bfloat16 *in, const __nv_bfloat16 *dout, int l) {
+  const int nblk = (int)(g.nbricks < ws->nsm ? g.nbricks : ws->nsm);
+  const size_t need = (size_t)nblk * (NTAP * COUT * CIN + COUT);
+  int rc = ensure_part(ws, need);
+  if (rc) return rc;
+  WgArgs a{g, in, dout, ws->part, ws->part + (size_t)nblk * NTAP * COUT * CIN};
+  k_wgrad<CIN, COUT><<<nblk, WG_THREADS, wgrad_smem_bytes<CIN, COUT>(), ws->stream>>>(a);
+  const int nout = L_COUT[l] * L_CIN[l] * NTAP + L_COUT[l];
+  k_wgrad_reduce<<<(nout + EW - 1) / EW, EW, 0, ws->stream>>>(nblk, CIN, COUT, L_CIN[l], L_COUT[l], a.part, a.partb,
+                                                             ws->grad + ws->woff[l], ws->grad + ws->boff[l]);
+  ws->launches += 2;
+  return RKL_OK;
+}
+
+// buffers of one pass over `cells` cells, carved from the arena (256-byte aligned)
+struct Bufs {
+  __nv_bfloat16 *a0, *a1, *a2, *a3, *dy, *dzA, *dzB;
+  float *y;
+};
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+int carve(rkl_ws *ws, long long cells, bool training, Bufs &b) {
+  const size_t s16 = align256((size_t)cells * 16 * 2), s32 = align256((size_t)cells * 32 * 2),
+               sf = align256((size_t)cells * 4);
+  const size_t total = training ? (2 * s16 + 5 * s32 + sf) : (s16 + 2 * s32 + sf);
+  int rc = ensure_arena(ws, total);
+  if (rc) return rc;
+  unsigned char *p = ws->arena;
+  auto take = [&](size_t s) {
+    unsigned char *q = p;
+    p += s;
+    return q;
+  };
+  b.a0 = (__nv_bfloat16 *)take(s16);
+  b.a1 = (__nv_bfloat16 *)take(s32);
+  b.a2 = (__nv_bfloat16 *)take(s32);
+  if (training) {
+    b.a3 = (__nv_bfloat16 *)take(s32);
+    b.dy = (__nv_bfloat16 *)take(s16);
+    b.dzA = (__nv_bfloat16 *)take(s32);
+    b.dzB = (__nv_bfloat16 *)take(s32);
+  } else {
+    b.a3 = b.a1;  // a1 is dead once a2 exists
+    b.dy = b.dzA = b.dzB = nullptr;
+  }
+  b.y = (float *)take(sf);
+  return RKL_OK;
+}
+
+void run_forward(rkl_ws *ws, const Boxes &g, const Bufs &b) {
+  launch_conv<16, 4, EPI_RELU>(ws, g, b.a0, ws->wfrag[0], ws->param + ws->boff[0], nullptr, b.a1);
+  launch_conv<32, 4, EPI_RELU>(ws, g, b.a1, ws->wfrag[1], ws->param + ws->boff[1], nullptr, b.a2);
+  launch_conv<32, 4, EPI_RELU>(ws, g, b.a2, ws->wfrag[2], ws->param + ws->boff[2], nullptr, b.a3);
+  launch_conv<32, 1, EPI_F32>(ws, g, b.a3, ws->wfrag[3], ws->param + ws->boff[3], nullptr, b.y);
+}
+
+bool valid_box(const int box[3], int nbox) {
+  return box && nbox >= 1 && box[0] >= 1 && box[1] >= 1 && box[2] >= 1;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ws_num_params(void) {
+  int n = 0;
+  for (int l = 0; l < NL; l++) n += L_COUT[l] * L_CIN[l] * NTAP + L_COUT[l];
+  return n;
+}
+
+int ws_create(rkl_ws **out, unsigned long long seed, void *cuda_stream) {
+  if (!out) return RKL_EINVAL;
+  *out = nullptr;
+  rkl_ws *ws = new (std::nothrow) rkl_ws();
+  if (!ws) return RKL_ENOMEM;
+  ws->stream = (cudaStream_t)cuda_stream;
+  size_t off = 0, boff = 0;
+  for (int l = 0; l < NL; l++) {
+    ws->woff[l] = off;
+    ws->boff[l] = off + (size_t)L_COUT[l] * L_CIN[l] * NTAP;
+    ws->bw_off[l] = boff;
+    off = ws->boff[l] + L_COUT[l];
+    boff += (size_t)L_COUT[l] * L_CIN[l] * NTAP;
+  }
+  ws->nparam = (int)off;
+  ws->nweight = (int)boff;
+  int dev = 0;
+  int rc = ws_cuda(ws, cudaGetDevice(&dev));
+  if (!rc) rc = ws_cuda(ws, cudaDeviceGetAttribute(&ws->nsm, cudaDevAttrMultiProcessorCount, dev));
+  const size_t pb = sizeof(float) * ws->nparam;
+  if (!rc) rc = ws_cuda(ws, cudaMalloc(&ws->param, pb));
+  if (!rc) rc = ws_cuda(ws, cudaMalloc(&ws->grad, pb));
+  if (!rc) rc = ws_cuda(ws, cudaMalloc(&ws->m, pb));
+  if (!rc) rc = ws_cuda(ws, cudaMalloc(&ws->v, pb));
+  if (!rc) rc = ws_cuda(ws, cudaMalloc(&ws->wbf, sizeof(__nv_bfloat16) * ws->nweight));
+  if (!rc) rc = ws_cuda(ws, cudaMalloc(&ws->red, sizeof(double) * 2 * RED_BLOCKS));
+  for (int l = 0; l < NL && !rc; l++) {
+    rc = ws_cuda(ws, cudaMalloc(&ws->wfrag[l], sizeof(uint2) * frag_count(l)));
+    if (!rc && l > 0) rc = ws_cuda(ws, cudaMalloc(&ws->wadj[l], sizeof(uint2) * adj_count(l)));
+  }
+  if (!rc) rc = configure_kernels(ws);
+  if (!rc) {
+    std::vector<float> p(ws->nparam, 0.0f);
+    for (int l = 0; l < NL; l++) {
+      const size_t nw = (size_t)L_COUT[l] * L_CIN[l] * NTAP;
+      const double a = std::sqrt(6.0 / (L_CIN[l] * (double)NTAP));
+      for (size_t q = 0; q < nw; q++)
+        p[ws->woff[l] + q] = (float)((2.0 * splitmix_uniform(seed, ws->woff[l] + q) - 1.0) * a);
+    }
+    rc = ws_set_params(ws, p.data(), ws->nparam);
+  }
+  if (!rc) rc = ws_cuda(ws, cudaMemsetAsync(ws->grad, 0, pb, ws->stream));
+  if (rc) {
+    ws_destroy(ws);
+    return rc;
+  }
+  *out = ws;
+  return RKL_OK;
+}
+
+int ws_destroy(rkl_ws *ws) {
+  if (!ws) return RKL_OK;
+  cudaStreamSynchronize(ws->stream);
+  void *bufs[] = {ws->param, ws->grad, ws->m, ws->v, ws->wbf, ws->arena, ws->part, ws->red};
+  for (void *b : bufs)
+    if (b) cudaFree(b);
+  for (int l = 0; l < NL; l++) {
+    if (ws->wfrag[l]) cudaFree(ws->wfrag[l]);
+    if (ws->wadj[l]) cudaFree(ws->wadj[l]);
+  }
+  cudaGetLastError();
+  delete ws;
+  return RKL_OK;
+}
+
+const char *ws_last_error(const rkl_ws *ws) { return ws ? ws->err : ""; }
+
+long long ws_kernel_launches(const rkl_ws *ws) { return ws ? ws->launches : 0; }
+
+int ws_set_stream(rkl_ws *ws, void *cuda_stream) {
+  if (!ws) return RKL_EINVAL;
+  ws->stream = (cudaStream_t)cuda_stream;
+  return RKL_OK;
+}
+
+int ws_set_params(rkl_ws *ws, const float *params, int n) {
+  if (!ws || !params || n != ws->nparam) return RKL_EINVAL;
+  const size_t pb = sizeof(float) * n;
+  int rc = ws_cuda(ws, cudaMemcpyAsync(ws->param, params, pb, cudaMemcpyDefault, ws->stream));
+  if (!rc) rc = ws_cuda(ws, cudaMemsetAsync(ws->m, 0, pb, ws->stream));
+  if (!rc) rc = ws_cuda(ws, cudaMemsetAsync(ws->v, 0, pb, ws->stream));
+  if (!rc) rc = refresh_weights(ws);
+  if (!rc) rc = ws_cuda(ws, cudaStreamSynchronize(ws->stream));
+  ws->step = 0;
+  return rc;
+}
+
+int ws_get_params(rkl_ws *ws, float *params, int n) {
+  if (!ws || !params || n != ws->nparam) return RKL_EINVAL;
+  int rc = ws_cuda(ws, cudaMemcpyAsync(params, ws->param, sizeof(float) * n, cudaMemcpyDefault, ws->stream));
+  if (!rc) rc = ws_cuda(ws, cudaStreamSynchronize(ws->stream));
+  return rc;
+}
+
+int ws_get_grads(rkl_ws *ws, float *grads, int n) {
+  if (!ws || !grads || n != ws->nparam) return RKL_EINVAL;
+  int rc = ws_cuda(ws, cudaMemcpyAsync(grads, ws->grad, sizeof(float) * n, cudaMemcpyDefault, ws->stream));
+  if (!rc) rc = ws_cuda(ws, cudaStreamSynchronize(ws->stream));
+  return rc;
+}
+
+int ws_set_grads(rkl_ws *ws, const float *grads, int n) {
+  if (!ws || !grads || n != ws->nparam) return RKL_EINVAL;
+  return ws_cuda(ws, cudaMemcpyAsync(ws->grad, grads, sizeof(float) * n, cudaMemcpyDefault, ws->stream));
+}
+
+int ws_forward(rkl_ws *ws, const int box[3], int nbox, int periodic_phi, const float *in, float *out) {
+  if (!ws || !valid_box(box, nbox) || !in || !out) return RKL_EINVAL;
+  const Boxes g = make_boxes(box[0], box[1], box[2], nbox, periodic_phi ? 1 : 0);
+  const long long cells = g.nc * nbox;
+  Bufs b;
+  int rc = carve(ws, cells, false, b);
+  if (rc) return rc;
+  k_pack_input<<<(unsigned)((cells + EW - 1) / EW), EW, 0, ws->stream>>>(cells, in, b.a0);
+  ws->launches += 1;
+  Bufs o = b;
+  o.y = out;
+  run_forward(ws, g, o);
+  return ws_cuda(ws, cudaGetLastError());
+}
+
+int ws_loss_grad(rkl_ws *ws, const int box[3], int nbox, int periodic_phi, const float *in, const float *target,
+                 const float *weight, double *loss_out) {
+  if (!ws || !valid_box(box, nbox) || !in || !target) return RKL_EINVAL;
+  const Boxes g = make_boxes(box[0], box[1], box[2], nbox, periodic_phi ? 1 : 0);
+  const long long cells = g.nc * nbox;
+  Bufs b;
+  int rc = carve(ws, cells, true, b);
+  if (rc) return rc;
+  const unsigned eg = (unsigned)((cells + EW - 1) / EW);
+  k_pack_input<<<eg, EW, 0, ws->stream>>>(cells, in, b.a0);
+  run_forward(ws, g, b);
+  k_sum<<<RED_BLOCKS, EW, 0, ws->stream>>>(cells, weight, ws->red);
+  k_loss<<<RED_BLOCKS, EW, 0, ws->stream>>>(cells, b.y, target, weight, ws->red, RED_BLOCKS, b.dy,
+                                            ws->red + RED_BLOCKS);
+  ws->launches += 3;
+  // layer 4: dW4 from (dy, a3); dz3 = W4^T dy masked by a3 > 0
+  if ((rc = launch_wgrad<32, 16>(ws, g, b.a3, b.dy, 3))) return rc;
+  launch_conv<16, 4, EPI_MASK>(ws, g, b.dy, ws->wadj[3], nullptr, b.a3, b.dzA);
+  // layer 3: dW3 from (dz3, a2); dz2 = W3^T dz3 masked by a2 > 0
+  if ((rc = launch_wgrad<32, 32>(ws, g, b.a2, b.dzA, 2))) return rc;
+  launch_conv<32, 4, EPI_MASK>(ws, g, b.dzA, ws->wadj[2], nullptr, b.a2, b.dzB);
+  // layer 2: dW2 from (dz2, a1); dz1 = W2^T dz2 masked by a1 > 0
+  if ((rc = launch_wgrad<32, 32>(ws, g, b.a1, b.dzB, 1))) return rc;
+  launch_conv<32, 4, EPI_MASK>(ws, g, b.dzB, ws->wadj[1], nullptr, b.a1, b.dzA);
+  // layer 1: dW1 from (dz1, a0)
+  if ((rc = launch_wgrad<16, 32>(ws, g, b.a0, b.dzA, 0))) return rc;
+  if ((rc = ws_cuda(ws, cudaGetLastError()))) return rc;
+  if (loss_out) {
+    std::vector<double> h(2 * RED_BLOCKS);
+    rc = ws_cuda(ws, cudaMemcpyAsync(h.data(), ws->red, sizeof(double) * 2 * RED_BLOCKS, cudaMemcpyDeviceToHost,
+                                     ws->stream));
+    if (!rc) rc = ws_cuda(ws, cudaStreamSynchronize(ws->stream));
+    if (rc) return rc;
+    double wsum = 0.0, l = 0.0;
+    for (int q = 0; q < RED_BLOCKS; q++) wsum += h[q];
+    for (int q = 0; q < RED_BLOCKS; q++) l += h[RED_BLOCKS + q];
+    *loss_out = l / wsum;
+  }
+  return RKL_OK;
+}
+
+int ws_adam(rkl_ws *ws, double lr) {
+  if (!ws || !(lr > 0.0) || !std::isfinite(lr)) return RKL_EINVAL;
+  ws->step += 1;
+  const double b1 = 0.9, b2 = 0.999;
+  const float c1 = (float)(1.0 - std::pow(b1, (double)ws->step));
+  const float c2 = (float)(1.0 - std::pow(b2, (double)ws->step));
+  k_adam<<<(ws->nparam + EW - 1) / EW, EW, 0, ws->stream>>>(ws->nparam, ws->param, ws->grad, ws->m, ws->v, (float)lr,
+                                                           (float)b1, (float)(1.0 - b1), (float)b2,
+                                                           (float)(1.0 - b2), 1e-8f, c1, c2);
+  ws->launches += 1;
+  int rc = ws_cuda(ws, cudaGetLastError());
+  if (!rc) rc = refresh_weights(ws);
+  return rc;
+}
+
+int ws_features(rkl_ws *ws, const rkl_grid *grid, const double *T, const double *bhat, double dt, float *feat) {
+  if (!ws || !grid || grid->nr < 1 || grid->nth < 1 || grid->nph < 1 || !T || !bhat || !feat || !(dt > 0.0) ||
+      !std::isfinite(dt))
+    return RKL_EINVAL;
+  const long long N = (long long)grid->nr * grid->nth * grid->nph;
+  Bufs b;
+  int rc = carve(ws, N, false, b);
+  if (rc) return rc;
+  k_features<<<(unsigned)((N + EW - 1) / EW), EW, 0, ws->stream>>>(N, T, bhat, (float)std::log10(dt), b.a0, feat);
+  ws->launches += 1;
+  return ws_cuda(ws, cudaGetLastError());
+}
+
+int ws_guess(rkl_ws *ws, const rkl_grid *grid, const double *T, const double *bhat, double dt, double scale,
+             double *x0) {
+  if (!ws || !grid || grid->nr < 1 || grid->nth < 1 || grid->nph < 1 || !T || !bhat || !x0 || !(dt > 0.0) ||
+      !std::isfinite(dt) || !std::isfinite(scale))
+    return RKL_EINVAL;
+  const long long N = (long long)grid->nr * grid->nth * grid->nph;
+  const Boxes g = make_boxes(grid->nr, grid->nth, grid->nph, 1, 1);
+  Bufs b;
+  int rc = carve(ws, N, false, b);
+  if (rc) return rc;
+  const unsigned eg = (unsigned)((N + EW - 1) / EW);
+  k_features<<<eg, EW, 0, ws->stream>>>(N, T, bhat, (float)std::log10(dt), b.a0, nullptr);
+  run_forward(ws, g, b);
+  k_guess<<<eg, EW, 0, ws->stream>>>(N, T, b.y, scale, x0);
+  ws->launches += 2;
+  return ws_cuda(ws, cudaGetLastError());
+}
+
+int ws_target(rkl_ws *ws, long long n, const double *x, const double *base, double unit, float *target) {
+  if (!ws || n < 1 || !x || !base || !target || !(unit > 0.0) || !std::isfinite(unit)) return RKL_EINVAL;
+  k_target<<<(unsigned)((n + EW - 1) / EW), EW, 0, ws->stream>>>(n, x, base, 1.0 / unit, target);
+  ws->launches += 1;
+  return ws_cuda(ws, cudaGetLastError());
+}
+
+}  // extern "C"

@@ -27,13 +27,13 @@ def test_header_declares_the_boundary():
 
 def test_library_exports_every_declared_symbol():
     from paper_1610_01265_gb300 import build as B
-    from paper_1610_01265_gb300 import rklpcg
+    from paper_1610_01265_gb300 import rklpcg, warmstart
 
     path = B.build()
     lib = ctypes.CDLL(path)
     for name in declared_functions():
         assert hasattr(lib, name), f"{name} declared in include/ but not exported"
-    assert set(rklpcg.EXPORTED) == declared_functions()
+    assert set(rklpcg.EXPORTED) | set(warmstart.EXPORTED) == declared_functions()
 
 
 def test_host_only_calls_without_gpu():
@@ -47,3 +47,6 @@ def test_host_only_calls_without_gpu():
     lib = rklpcg.load()
     assert lib.rkl2_stage_count(-1.0, 0) == rklpcg.RKL_EINVAL
     assert lib.rkl2_stage_count(float("nan"), 0) == rklpcg.RKL_EINVAL
+    from paper_1610_01265_gb300 import warmstart
+
+    assert warmstart.num_params() == sum(co * ci * 27 + co for ci, co in warmstart.LAYERS) == 60577
