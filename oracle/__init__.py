@@ -116,12 +116,13 @@ def num_threads() -> int:
 
 
 def assemble_conduction(g: Grid, T, bhat, n, kappa0: float = 9e-7, beta_tcut: bool = False,
-                        isotropic: bool = False):
-    """S (N,19) = Hessian of the discrete energy, W (N,) = 3 k_B n V."""
+                        isotropic: bool = False, flux_form: bool = False):
+    """S (N,19) = Hessian of the discrete energy (flux_form: minus the divergence of the
+    face fluxes, non-symmetric, whose symmetric part is that Hessian), W (N,) = 3 k_B n V."""
     T, bhat, n = _f64(T), _f64(bhat), _f64(n)
     S = np.empty((g.N, NSLOT))
     W = np.empty(g.N)
-    flags = (1 if beta_tcut else 0) | (2 if isotropic else 0)
+    flags = (1 if beta_tcut else 0) | (2 if isotropic else 0) | (4 if flux_form else 0)
     rc = _load().or_assemble_conduction(*g._dims(), _ptr(T), _ptr(bhat), _ptr(n), kappa0, flags,
                                         _ptr(S), _ptr(W))
     if rc != 0:

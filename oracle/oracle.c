@@ -193,7 +193,11 @@ static int face_cells(const grid *g, int a, int i, int j, int k, int *L, int *R)
 
 /*
  * Conduction: assemble S = Hessian of Q (19 slots per row, zeroed here) and
- * W = 3 k_B n V.  flags: bit0 = beta_Tcut, bit1 = isotropic test hook (bhat bhat^T -> I).
+ * W = 3 k_B n V.  flags: bit0 = beta_Tcut, bit1 = isotropic test hook (bhat bhat^T -> I),
+ * bit2 = flux form: row c is minus the divergence of the face fluxes
+ * A_f (D_f^aa g_f + sum_{b!=a} D_f^ab ghat_b(f)) through the faces of c, the "standard"
+ * non-symmetric scheme whose symmetric part is the Hessian of Q (Sec. 4.2; PCG is used
+ * for such slightly non-symmetric operators, Sec. 2.1).
  */
 int or_assemble_conduction(int nr, int nth, int nph, const double *rf, const double *T,
                            const double *bhat, const double *n, double kappa0, int flags,
@@ -244,10 +248,18 @@ int or_assemble_conduction(int nr, int nth, int nph, const double *rf, const dou
             for (int x = 0; x < 4; x++) {
               double vL = coef * (-1.0) * w[x];
               double vR = coef * (+1.0) * w[x];
-              add_entry(&g, S, L, X[x], vL);
-              add_entry(&g, S, X[x], L, vL);
-              add_entry(&g, S, R, X[x], vR);
-              add_entry(&g, S, X[x], R, vR);
+              if (flags & 4) {
+                /* flux form: the face flux A_f (D^aa g + sum_b D^ab ghat_b) enters the rows
+                   of L and R only (the divergence of the flux), so the cross terms are not
+                   mirrored into the rows of the ghat_b neighbours */
+                add_entry(&g, S, L, X[x], 2.0 * vL);
+                add_entry(&g, S, R, X[x], 2.0 * vR);
+              } else {
+                add_entry(&g, S, L, X[x], vL);
+                add_entry(&g, S, X[x], L, vL);
+                add_entry(&g, S, R, X[x], vR);
+                add_entry(&g, S, X[x], R, vR);
+              }
             }
           }
         }
