@@ -38,6 +38,7 @@ VISC_RATIO = 500.0
 RTOL = 1e-10
 MAXIT = 20000
 BLOCK = (8, 8, 8)
+BETA_TCUT = True  # conduction coefficient evaluated at max(T, 5e5 K), as in the paper's runs (Sec. 4.1)
 FP64_PEAK_TFLOPS = 1.25  # nominal FP64 rate of the GB300 (2 DFMA/clk/SM x 152 SMs x 2.07 GHz)
 # Algorithmic cost per cell of one launch of each kernel family (one field component):
 # (flop, bytes, binding unit, ncu summary, sources the summary was taken on).
@@ -69,6 +70,8 @@ def parse_args():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-accuracy", action="store_true")
     p.add_argument("--seed", type=int, default=1)
+    p.add_argument("--mixed-large", action="store_true",
+                   help="run the mixed-precision comparison at 256x384x768 (75.5 M cells) instead of the step")
     p.add_argument("--warmstart", action="store_true",
                    help="run the learned-initial-guess study (200 BE steps with heating) instead of the step")
     p.add_argument("--profile", choices=("stage", "apply", "pcg-jacobi", "pcg-bilu0", "setup", "stage-mix",
@@ -93,6 +96,7 @@ def base_config():
         "be_dt_over_dt_exp": list(RATIOS),
         "pcg": ["jacobi", "bilu0-8x8x8"],
         "rtol": RTOL,
+        "beta_tcut": BETA_TCUT,
         "viscosity_dt_over_dt_exp": VISC_RATIO,
         "l2": "no flush: every stage pass streams ~1.2 GB, far above the 129 MB L2",
     }
@@ -110,7 +114,7 @@ def cpu_sample(seed: int):
     nr, nth, nph = GRID
     c = synth.conduction_case(nr, nth, nph, seed)
     g = O.Grid(c["rf"], nth, nph)
-    S, W = O.assemble_conduction(g, c["T"], c["bhat"], c["n"])
+    S, W = O.assemble_conduction(g, c["T"], c["bhat"], c["n"], beta_tcut=BETA_TCUT)
     dte, _ = O.gershgorin_dt(g, S, W)
 
     def run():
@@ -291,7 +295,7 @@ class Workload:
         units = 0
         info = {"rkl2": {}, "be": {}, "visc": {}}
         self.h2d = self.d2h = 0
-        dte = self.ctx_c.set_conduction(self.T, self.b, self.n)
+        dte = self.ctx_c.set_conduction(self.T, self.b, self.n, beta_tcut=BETA_TCUT)
         self.h2d += 5 * N * 8
         for ratio in RATIOS:
             self._load(self.u, self.T)
@@ -339,9 +343,9 @@ def path_timings(wl, torch):
     R = wl.R
     out = {}
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    dte = wl.ctx_c.set_conduction(wl.T, wl.b, wl.n)
+    dte = wl.ctx_c.set_conduction(wl.T, wl.b, wl.n, beta_tcut=BETA_TCUT)
     e0.record()
-    wl.ctx_c.set_conduction(wl.T, wl.b, wl.n)
+    wl.ctx_c.set_conduction(wl.T, wl.b, wl.n, beta_tcut=BETA_TCUT)
     e1.record()
     torch.cuda.synchronize()
     out["set_coeffs_conduction_ms"] = e0.elapsed_time(e1)
@@ -372,8 +376,8 @@ def mixed_report(wl, R, torch):
     out = {}
     mix = R.Context(wl.ctx_c._rf, nth, nph, prec=R.RKL_F32MIX)
     try:
-        dte = mix.set_conduction(wl.T, wl.b, wl.n)
-        wl.ctx_c.set_conduction(wl.T, wl.b, wl.n)
+        dte = mix.set_conduction(wl.T, wl.b, wl.n, beta_tcut=BETA_TCUT)
+        wl.ctx_c.set_conduction(wl.T, wl.b, wl.n, beta_tcut=BETA_TCUT)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ref = torch.empty_like(wl.T)
         for ratio in RATIOS:
@@ -404,10 +408,44 @@ def mixed_report(wl, R, torch):
     return out
 
 
+def flux_report(wl, torch):
+    """The non-symmetric flux form of conduction (RKL_FLUX_FORM) next to the symmetric form
+    on the same inputs: ms per large step and PCG iterations (RKL2 and block-ILU0 PCG at
+    dt = 1000 dt_exp, Jacobi PCG at 30 and, capped, at 1000 dt_exp)."""
+    R = wl.R
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {}
+    for name, flux in (("symmetric", False), ("flux_form", True)):
+        e0.record()
+        dte = wl.ctx_c.set_conduction(wl.T, wl.b, wl.n, beta_tcut=BETA_TCUT, flux_form=flux)
+        e1.record()
+        torch.cuda.synchronize()
+        r = {"set_coeffs_ms": e0.elapsed_time(e1), "dt_exp_s": dte}
+        wl.u.copy_(wl.T)
+        e0.record()
+        s = wl.ctx_c.rkl2_superstep(wl.u, 1000 * dte, dte)
+        e1.record()
+        torch.cuda.synchronize()
+        r["rkl2_1000"] = {"s": s, "ms": e0.elapsed_time(e1)}
+        # point Jacobi stalls on the flux form at large dt: capped at 2000 iterations there
+        for pc, pname, ratio, maxit in ((R.RKL_PC_JACOBI, "jacobi", 30, MAXIT), (R.RKL_PC_JACOBI, "jacobi", 1000, 2000),
+                                        (R.RKL_PC_BILU0, "bilu0", 1000, MAXIT)):
+            wl.u.copy_(wl.T)
+            e0.record()
+            code, its, rel = wl.ctx_c.be_pcg_solve(wl.u, ratio * dte, pc=pc, block=BLOCK, rtol=RTOL, maxit=maxit)
+            e1.record()
+            torch.cuda.synchronize()
+            r[f"be_{pname}_{ratio}"] = {"iters": its[0], "ms": e0.elapsed_time(e1), "relres": rel[0],
+                                        "converged": code == R.RKL_OK}
+        out[name] = r
+    wl.ctx_c.set_conduction(wl.T, wl.b, wl.n, beta_tcut=BETA_TCUT)
+    return out
+
+
 def variants_report(wl, torch):
     """Sec. 6 remedies at dt = 1000 dt_exp: cost of 10 RKL2 sub-cycles and of an explicit
     Euler prefix over a quarter of the step, next to one RKL2 super-step."""
-    dte = wl.ctx_c.set_conduction(wl.T, wl.b, wl.n)
+    dte = wl.ctx_c.set_conduction(wl.T, wl.b, wl.n, beta_tcut=BETA_TCUT)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     out = {}
     for name, kw in (("rkl2", {}), ("rkl2_10_cycles", {"cycles": 10}), ("euler_prefix_0.25", {"euler_fraction": 0.25}),
@@ -425,7 +463,7 @@ def accuracy_report(wl, torch):
     """Relative L2 error of one large step of each method against the semi-discrete
     solution exp(dt M) T, approximated by 64 RKL2 sub-steps of dt/64 (FP64 GPU path)."""
     R = wl.R
-    dte = wl.ctx_c.set_conduction(wl.T, wl.b, wl.n)
+    dte = wl.ctx_c.set_conduction(wl.T, wl.b, wl.n, beta_tcut=BETA_TCUT)
     out = {}
     for ratio in RATIOS:
         ref = wl.T.clone()
@@ -506,7 +544,7 @@ def profile_case(args):
         return 0
     mixed = args.profile.endswith("-mix")
     ctx = R.Context(c["rf"], nth, nph, prec=R.RKL_F32MIX if mixed else R.RKL_F64)
-    dte = ctx.set_conduction(T, b, n)
+    dte = ctx.set_conduction(T, b, n, beta_tcut=BETA_TCUT)
     u = T.clone()
     if args.profile in ("stage", "stage-mix"):
         ctx.rkl2_superstep(u, 10 * dte, dte, s=4)
@@ -519,11 +557,87 @@ def profile_case(args):
     elif args.profile == "pcg-bilu0":
         ctx.be_pcg_solve(u, 100 * dte, pc=R.RKL_PC_BILU0, block=BLOCK, rtol=0.0, maxit=3)
     elif args.profile == "setup":
-        ctx.set_conduction(T, b, n)
+        ctx.set_conduction(T, b, n, beta_tcut=BETA_TCUT)
     torch.cuda.synchronize()
     ctx.close()
     print(f"profile case {args.profile} done")
     return 0
+
+
+# ------------------------------------------------------------------ mixed precision, 75.5 M cells
+MIXED_GRID = (256, 384, 768)
+
+
+def mixed_large_report(seed=1, dims=MIXED_GRID, ratios=RATIOS, log=None):
+    """FP32-stage / FP32-PCG path against the FP64 path at 256 x 384 x 768: ms per large
+    step, cell-updates/s and the relative L2 difference per large step, plus the live
+    roofline of the FP32 stage kernel (60 B per cell: 10 FP32 coefficients, 1/W, three
+    increments read, one written)."""
+    import torch
+
+    from paper_1610_01265_gb300 import rklpcg as R
+    from paper_1610_01265_gb300 import synth
+
+    nr, nth, nph = dims
+    N = nr * nth * nph
+    c = synth.conduction_case(nr, nth, nph, seed)
+    dev = lambda a: torch.from_numpy(np.array(a, dtype=np.float64).ravel()).cuda()  # noqa: E731
+    T, b, n = dev(c["T"]), dev(c["bhat"]), dev(c["n"])
+    del c
+    ctx64 = R.Context(synth.r_faces(nr), nth, nph)
+    mix = R.Context(synth.r_faces(nr), nth, nph, prec=R.RKL_F32MIX)
+    dte = ctx64.set_conduction(T, b, n, beta_tcut=BETA_TCUT)
+    mix.set_conduction(T, b, n, beta_tcut=BETA_TCUT)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        e0.record()
+        r = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return r, e0.elapsed_time(e1)
+
+    out = {"grid_nr_nth_nph": list(dims), "cells": N, "beta_tcut": BETA_TCUT, "rtol": RTOL}
+    ref = torch.empty_like(T)
+    u = torch.empty_like(T)
+    for ratio in ratios:
+        dt = ratio * dte
+        ref.copy_(T)
+        s, ms64 = timed(lambda: ctx64.rkl2_superstep(ref, dt, dte))
+        u.copy_(T)
+        mix.rkl2_superstep(u, dt, dte)  # warm
+        u.copy_(T)
+        mix.profile_enable(True)
+        _, msm = timed(lambda: mix.rkl2_superstep(u, dt, dte))
+        prof = mix.profile()
+        mix.profile_enable(False)
+        chg = torch.linalg.vector_norm(ref - T).item()
+        r = {"s": s, "fp64_ms": ms64, "mixed_ms": msm, "fp64_cell_updates_per_s": N * s / ms64 * 1e3,
+             "mixed_cell_updates_per_s": N * s / msm * 1e3,
+             "err_rel_change": torch.linalg.vector_norm(u - ref).item() / chg,
+             "err_rel_u": torch.linalg.vector_norm(u - ref).item() / torch.linalg.vector_norm(ref).item()}
+        st_ms, st_n = prof.get("rkl2_stage", (0.0, 0))
+        if st_n:
+            t = st_ms / st_n * 1e-3
+            r["stage_kernel"] = {"launch_ms": t * 1e3, "hbm_gbs": 60.0 * N / t / 1e9,
+                                 "hbm_frac": 60.0 * N / t / 1e9 / measured_peaks().get("hbm_gbs", 6800.0)}
+        for pc, name in ((R.RKL_PC_JACOBI, "jacobi"), (R.RKL_PC_BILU0, "bilu0")):
+            ref.copy_(T)
+            (code64, its64, _), b64 = timed(lambda: ctx64.be_pcg_solve(ref, dt, pc=pc, block=BLOCK, rtol=RTOL,
+                                                                        maxit=MAXIT))
+            u.copy_(T)
+            (codem, itsm, relm), bm = timed(lambda: mix.be_pcg_solve(u, dt, pc=pc, block=BLOCK, rtol=RTOL,
+                                                                     maxit=MAXIT))
+            r[f"be_{name}"] = {"fp64_iters": its64[0], "fp64_ms": b64, "mixed_fp32_iters": itsm[0], "mixed_ms": bm,
+                               "mixed_relres_fp64": relm[0], "converged": code64 == R.RKL_OK and codem == R.RKL_OK,
+                               "err_rel_change": torch.linalg.vector_norm(u - ref).item()
+                               / torch.linalg.vector_norm(ref - T).item()}
+        out[str(int(ratio))] = r
+        if log:
+            log(f"ratio {ratio}: {r}")
+    ctx64.close()
+    mix.close()
+    return out
 
 
 # ------------------------------------------------------------------ learned initial guess
@@ -551,7 +665,7 @@ def warmstart_study(seed=1, dims=GRID, n_steps=WS_STEPS, n_train=WS_TRAIN, ratio
     dev = lambda a: torch.from_numpy(np.array(a, dtype=np.float64).ravel()).cuda()  # noqa: E731
     T, b, n, h = dev(c["T"]), dev(c["bhat"]), dev(c["n"]), dev(hc["h"])
     ctx = R.Context(c["rf"], nth, nph)
-    dt = ratio * ctx.set_conduction(T, b, n)
+    dt = ratio * ctx.set_conduction(T, b, n, beta_tcut=BETA_TCUT)
     net = W.Net(seed)
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
 
@@ -562,7 +676,7 @@ def warmstart_study(seed=1, dims=GRID, n_steps=WS_STEPS, n_train=WS_TRAIN, ratio
     ustars, targets = [], []
     train_iters = []
     for step in range(n_train):
-        ctx.set_conduction(T, b, n)
+        ctx.set_conduction(T, b, n, beta_tcut=BETA_TCUT)
         us = heated(T, step)
         x = us.clone()
         code, its, _ = ctx.be_pcg_solve(x, dt, pc=R.RKL_PC_JACOBI, rtol=RTOL, maxit=MAXIT)
@@ -604,7 +718,7 @@ def warmstart_study(seed=1, dims=GRID, n_steps=WS_STEPS, n_train=WS_TRAIN, ratio
     x0 = torch.empty_like(T)
     test_loss = []
     for step in range(n_train, n_steps):
-        ctx.set_conduction(T, b, n)
+        ctx.set_conduction(T, b, n, beta_tcut=BETA_TCUT)
         us = heated(T, step)
         sols = {}
         for pc in pcs:
@@ -700,6 +814,17 @@ def main():
         return run_reference(args)
     if args.profile:
         return profile_case(args)
+    if args.mixed_large:
+        import torch
+
+        from paper_1610_01265_gb300 import build as B
+
+        B.build()
+        if not torch.cuda.is_available():
+            raise SystemExit("bench.py needs a CUDA GPU")
+        print(json.dumps(mixed_large_report(args.seed, log=lambda m: print(m, file=sys.stderr, flush=True))),
+              flush=True)
+        return 0
     if args.warmstart:
         import torch
 
@@ -820,6 +945,7 @@ def main():
             detail["accuracy_vs_semidiscrete"] = accuracy_report(wl, torch)
             detail["mixed_precision"] = mixed_report(wl, R, torch)
             detail["sec6_variants"] = variants_report(wl, torch)
+            detail["flux_form"] = flux_report(wl, torch)
 
     e2e = None
     if not args.no_e2e:

@@ -64,6 +64,7 @@ enum { RKL_PC_JACOBI = 1, RKL_PC_BILU0 = 2 };
 enum { RKL_F64 = 0, RKL_F32MIX = 1 };
 
 #define RKL_BETA_TCUT 1 /* set_coeffs: evaluate kappa at max(T, 5e5 K) (Sec. 4.1 beta_Tcut) */
+#define RKL_FLUX_FORM 2 /* set_coeffs (conduction): non-symmetric flux form, see set_coeffs */
 #define RKL_FORCE_ODD 1 /* rkl2_superstep: round s up to an odd number (Sec. 3) */
 
 /* Create a context for one grid on the current CUDA device.
@@ -127,9 +128,16 @@ int rkl2_stage_count(double dt_over_dt_exp, int flags);
  * dt_exp = 2 / max_i sum_j |M_ij| (App. B, Eqs. 6-7, Gershgorin row sums).
  *   op = RKL_OP_CONDUCTION: a = T [N] (K), b = bhat [3N] (r, theta, phi unit-vector
  *        components), c = n [N] (cm^-3), kappa0 (cgs, 9e-7 in the paper);
- *        flags may hold RKL_BETA_TCUT.
+ *        flags may hold RKL_BETA_TCUT and RKL_FLUX_FORM.  By default S is the
+ *        symmetric Hessian of the discrete energy; with RKL_FLUX_FORM row c is minus
+ *        the divergence of the face fluxes A_f (D^aa g_f + sum_b D^ab ghat_b) through
+ *        the faces of c (the "standard" scheme of Sec. 4.2), a non-symmetric operator
+ *        (about 7% antisymmetric on coronal fields) with the same symmetric part,
+ *        stored as full 19-entry rows (152 B per cell instead of 80).  Every solver
+ *        accepts it; PCG then runs as for "slightly non-symmetric" operators (Sec. 2.1)
+ *        and still stops on the true residual.  rkl2_superstep_noalloc does not.
  *   op = RKL_OP_VISCOSITY:  a = rho [N] (g cm^-3), b = NULL, c = nu [N] (cm^2/s);
- *        kappa0 and flags are ignored.
+ *        kappa0 is ignored; RKL_FLUX_FORM is RKL_EINVAL, other flags are ignored.
  * dt_exp_out (host, may be NULL) receives dt_exp in seconds.  Invalidates any
  * cached preconditioner.  RKL_ENONFINITE if an input is NaN/Inf or T, n, rho, nu <= 0. */
 int set_coeffs(rkl_ctx *ctx, int op, const double *a, const double *b, const double *c,
@@ -192,7 +200,8 @@ int be_pcg_solve(rkl_ctx *ctx, double *u, int ncomp, double dt, int pc, const in
  * library, about 12.6 MiB, which a GPU holds from its first use until the process exits;
  * hence nr <= 1024, nth <= 1024 and nr*nth*nph <= 65536 cells (RKL_EINVAL beyond).
  * T [N], bhat [3N], n [N] and u [N] must be device pointers (RKL_EINVAL otherwise); u is
- * advanced in place.  kappa0 and coeff_flags are those of set_coeffs; dt, s (0: Eq. 5
+ * advanced in place.  kappa0 and coeff_flags are those of set_coeffs (RKL_BETA_TCUT
+ * only: RKL_FLUX_FORM is RKL_EINVAL); dt, s (0: Eq. 5
  * with the dt_exp computed here) and flags those of rkl2_superstep.  dt_exp_out and
  * s_used (host, may be NULL) receive dt_exp and the number of stages.
  * The first call on a device looks up the device address of the static array with that

@@ -211,6 +211,7 @@ int rkl_create(rkl_ctx **out, const rkl_grid *g, int prec, void *stream) {
   if (!rc) rc = build_geometry(ctx);
   const size_t N = (size_t)ctx->d.N;
   if (!rc) rc = cuda_check(ctx, cudaMalloc(&ctx->coef, NCOEF_COND * N * sizeof(double)), "alloc coefficients");
+  if (!rc) ctx->coef_slots = NCOEF_COND;
   if (!rc) rc = cuda_check(ctx, cudaMalloc(&ctx->W, N * sizeof(double)), "alloc W");
   if (!rc) rc = cuda_check(ctx, cudaMalloc(&ctx->invW, N * sizeof(double)), "alloc 1/W");
   if (!rc) rc = cuda_check(ctx, cudaMalloc(&ctx->d_lammax, sizeof(unsigned long long) + 2 * sizeof(int)), "alloc flags");
@@ -268,11 +269,23 @@ int set_coeffs(rkl_ctx *ctx, int op, const double *a, const double *b, const dou
     return set_error(ctx, RKL_EINVAL, "set_coeffs: null input array");
   if (op == RKL_OP_CONDUCTION && !finite_pos(kappa0))
     return set_error(ctx, RKL_EINVAL, "set_coeffs: kappa0 must be finite and > 0");
+  if (op == RKL_OP_VISCOSITY && (flags & RKL_FLUX_FORM))
+    return set_error(ctx, RKL_EINVAL, "set_coeffs: the flux form is a conduction option");
   const size_t N = (size_t)ctx->d.N;
+  const int kind = (op == RKL_OP_CONDUCTION && (flags & RKL_FLUX_FORM)) ? OPK_FLUX : op;
   ctx->op = -1;
   ctx->lu_valid = 0;
   int rc = ensure_buffer(ctx, &ctx->scratch, 10 * N, "alloc set_coeffs scratch");
   if (rc) return rc;
+  if (op_ncoef(kind) > ctx->coef_slots) {  // full rows need 19 slots
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(ctx->coef);
+    ctx->coef = nullptr;
+    ctx->coef_slots = 0;
+    if ((rc = cuda_check(ctx, cudaMalloc(&ctx->coef, op_ncoef(kind) * N * sizeof(double)), "alloc coefficients")))
+      return rc;
+    ctx->coef_slots = op_ncoef(kind);
+  }
   double *da, *db = nullptr, *dc;
   bool sa, sb = false, sc;
   if (!is_device_ptr(a) || (b && !is_device_ptr(b)) || !is_device_ptr(c))
@@ -282,7 +295,7 @@ int set_coeffs(rkl_ctx *ctx, int op, const double *a, const double *b, const dou
   if ((rc = to_device(ctx, c, N, 4 * N, true, &dc, &sc))) return rc;
   if ((rc = cuda_check(ctx, cudaMemsetAsync(ctx->d_lammax, 0, sizeof(unsigned long long) + 2 * sizeof(int), ctx->stream), "clear flags")))
     return rc;
-  ctx->op = op;
+  ctx->op = kind;
   rc = op == RKL_OP_CONDUCTION ? launch_setup_conduction(ctx, da, db, dc, kappa0, flags)
                                : launch_setup_viscosity(ctx, da, dc);
   if (rc) {
@@ -309,8 +322,14 @@ int set_coeffs(rkl_ctx *ctx, int op, const double *a, const double *b, const dou
     return set_error(ctx, RKL_ECUDA, "set_coeffs: internal stencil assembly error");
   }
   if (ctx->prec == RKL_F32MIX) {  // FP32 copies of the frozen operator
-    const long long nslot = op == RKL_OP_CONDUCTION ? NCOEF_COND : NCOEF_VISC;
-    if ((rc = ensure_fbuffer(ctx, &ctx->coef32, NCOEF_COND * N, "alloc FP32 coefficients")) ||
+    const long long nslot = op_ncoef(kind);
+    if (nslot > ctx->coef32_slots && ctx->coef32) {
+      cudaStreamSynchronize(ctx->stream);
+      cudaFree(ctx->coef32);
+      ctx->coef32 = nullptr;
+    }
+    if (!ctx->coef32) ctx->coef32_slots = (int)std::max<long long>(nslot, NCOEF_COND);
+    if ((rc = ensure_fbuffer(ctx, &ctx->coef32, (size_t)ctx->coef32_slots * N, "alloc FP32 coefficients")) ||
         (rc = ensure_fbuffer(ctx, &ctx->W32, N, "alloc FP32 W")) ||
         (rc = ensure_fbuffer(ctx, &ctx->invW32, N, "alloc FP32 1/W")) ||
         (rc = launch_to_float(ctx, ctx->coef, ctx->coef32, nslot * (long long)N)) ||

@@ -11,6 +11,11 @@
 // walks every face that touches its row (its own 6 faces and the 24 faces for which
 // it is a transverse neighbour) and keeps the row in registers.
 //
+// Flux form (RKL_FLUX_FORM): row c is minus the divergence of the face fluxes
+// A_f (D_f^aa g_f + sum_b D_f^ab ghat_b) through the six faces of c -- the "standard",
+// slightly non-symmetric scheme whose symmetric part is the S above -- stored as full
+// 19-entry rows.
+//
 // Viscosity: Q_v = 1/2 sum_f Vt_f mu_f g_f^2 (7-point), mu = nu rho, W = rho V.
 #include <cuda_runtime.h>
 
@@ -141,8 +146,10 @@ __device__ __forceinline__ void add_sel(double (&row)[27], bool first, double v)
   else row[I0] += v;
 }
 
-// own face of c (c = L when SC = -1, c = R when SC = +1); L at offset (LI, LJ, LK)
-template <int A, int LI, int LJ, int LK, int SC>
+// own face of c (c = L when SC = -1, c = R when SC = +1); L at offset (LI, LJ, LK).
+// FLUX: the flux form takes the whole cross term of the face flux into the row (twice
+// the symmetric share; the transverse neighbours' rows get nothing).
+template <int A, int LI, int LJ, int LK, int SC, int FLUX>
 __device__ __forceinline__ void own_face(double (&row)[27], const RowCell &C, const Geo &g,
                                          const double *__restrict__ FS, long long N) {
   constexpr int RI = LI + ex_(A, 0), RJ = LJ + ex_(A, 1), RK = LK + ex_(A, 2);
@@ -154,7 +161,7 @@ __device__ __forceinline__ void own_face(double (&row)[27], const RowCell &C, co
 #pragma unroll
   for (int t = 0; t < 2; t++) {
     // (t is unrolled; tdir is constexpr-folded)
-    const double be = FS[(3 * A + 1 + t) * N + l];
+    const double be = (FLUX ? 2.0 : 1.0) * FS[(3 * A + 1 + t) * N + l];
     if (t == 0) {
       constexpr int B = tdir(A, 0), EI = ex_(B, 0), EJ = ex_(B, 1), EK = ex_(B, 2);
       const bool exp_ = has<EI, EJ, EK>(C), exm = has<-EI, -EJ, -EK>(C);
@@ -165,8 +172,10 @@ __device__ __forceinline__ void own_face(double (&row)[27], const RowCell &C, co
       add_sel<r27(RI + EI, RJ + EJ, RK + EK), r27(RI, RJ, RK)>(row, exp_, v * gr);
       add_sel<r27(RI - EI, RJ - EJ, RK - EK), r27(RI, RJ, RK)>(row, exm, -v * gr);
       const double wp = SC < 0 ? gl : gr, wm = SC < 0 ? -gl : -gr;  // ghosts of c itself
-      if (!exp_) { row[r27(LI, LJ, LK)] -= be * wp; row[r27(RI, RJ, RK)] += be * wp; }
-      if (!exm) { row[r27(LI, LJ, LK)] -= be * wm; row[r27(RI, RJ, RK)] += be * wm; }
+      // (column-side entries: c enters ghat_B of this face as its own mirror ghost; the
+      // flux form has no column-side entries)
+      if (!FLUX && !exp_) { row[r27(LI, LJ, LK)] -= be * wp; row[r27(RI, RJ, RK)] += be * wp; }
+      if (!FLUX && !exm) { row[r27(LI, LJ, LK)] -= be * wm; row[r27(RI, RJ, RK)] += be * wm; }
     } else {
       constexpr int B = tdir(A, 1), EI = ex_(B, 0), EJ = ex_(B, 1), EK = ex_(B, 2);
       const bool exp_ = has<EI, EJ, EK>(C), exm = has<-EI, -EJ, -EK>(C);
@@ -177,8 +186,8 @@ __device__ __forceinline__ void own_face(double (&row)[27], const RowCell &C, co
       add_sel<r27(RI + EI, RJ + EJ, RK + EK), r27(RI, RJ, RK)>(row, exp_, v * gr);
       add_sel<r27(RI - EI, RJ - EJ, RK - EK), r27(RI, RJ, RK)>(row, exm, -v * gr);
       const double wp = SC < 0 ? gl : gr, wm = SC < 0 ? -gl : -gr;
-      if (!exp_) { row[r27(LI, LJ, LK)] -= be * wp; row[r27(RI, RJ, RK)] += be * wp; }
-      if (!exm) { row[r27(LI, LJ, LK)] -= be * wm; row[r27(RI, RJ, RK)] += be * wm; }
+      if (!FLUX && !exp_) { row[r27(LI, LJ, LK)] -= be * wp; row[r27(RI, RJ, RK)] += be * wp; }
+      if (!FLUX && !exm) { row[r27(LI, LJ, LK)] -= be * wm; row[r27(RI, RJ, RK)] += be * wm; }
     }
   }
 }
@@ -201,11 +210,12 @@ __device__ __forceinline__ void trans_face(double (&row)[27], const RowCell &C, 
   row[r27(RI, RJ, RK)] += be * w;
 }
 
-template <int A>
+template <int A, int FLUX>
 __device__ __forceinline__ void faces_of_direction(double (&row)[27], const RowCell &C, const Geo &g,
                                                    const double *__restrict__ FS, long long N) {
-  own_face<A, 0, 0, 0, -1>(row, C, g, FS, N);
-  own_face<A, -ex_(A, 0), -ex_(A, 1), -ex_(A, 2), +1>(row, C, g, FS, N);
+  own_face<A, 0, 0, 0, -1, FLUX>(row, C, g, FS, N);
+  own_face<A, -ex_(A, 0), -ex_(A, 1), -ex_(A, 2), +1, FLUX>(row, C, g, FS, N);
+  if (FLUX) return;
   trans_face<A, 0, +1, 0>(row, C, g, FS, N);
   trans_face<A, 0, +1, 1>(row, C, g, FS, N);
   trans_face<A, 0, -1, 0>(row, C, g, FS, N);
@@ -216,6 +226,7 @@ __device__ __forceinline__ void faces_of_direction(double (&row)[27], const RowC
   trans_face<A, 1, -1, 1>(row, C, g, FS, N);
 }
 
+template <int FLUX>
 __global__ void __launch_bounds__(BLK) k_assemble_cond_fast(Dims d, Geo g, const double *__restrict__ FS,
                                                             const double *__restrict__ invW,
                                                             double *__restrict__ coef,
@@ -240,15 +251,19 @@ __global__ void __launch_bounds__(BLK) k_assemble_cond_fast(Dims d, Geo g, const
   double row[27];
 #pragma unroll
   for (int q = 0; q < 27; q++) row[q] = 0.0;
-  faces_of_direction<0>(row, C, g, FS, d.N);
-  faces_of_direction<1>(row, C, g, FS, d.N);
-  faces_of_direction<2>(row, C, g, FS, d.N);
+  faces_of_direction<0, FLUX>(row, C, g, FS, d.N);
+  faces_of_direction<1, FLUX>(row, C, g, FS, d.N);
+  faces_of_direction<2, FLUX>(row, C, g, FS, d.N);
   double sum = 0.0;
 #pragma unroll
   for (int q = 0; q < 27; q++) sum += fabs(row[q]);
 #pragma unroll
   for (int m = 0; m < 9; m++) coef[m * d.N + cl] = row[r27(fwd_di(m), fwd_dj(m), fwd_dk(m))];
   coef[9 * d.N + cl] = row[13];
+  if (FLUX) {  // full rows: the backward entries in slots 10..18
+#pragma unroll
+    for (int m = 0; m < 9; m++) coef[(10 + m) * d.N + cl] = row[r27(-fwd_di(m), -fwd_dj(m), -fwd_dk(m))];
+  }
   double rs = sum * invW[cl];
   if (!isfinite(rs)) atomicOr(flag, 1);
   else atomicMax(lammax, (unsigned long long)__double_as_longlong(rs));
@@ -328,8 +343,12 @@ int launch_setup_conduction(rkl_ctx *ctx, const double *T, const double *bhat, c
   k_cell_cond<<<grid, BLK, 0, ctx->stream>>>(d, ctx->geo, T, bhat, n, kappa0, flags, kappa, ctx->W,
                                             ctx->invW, ctx->d_flag);
   k_faces_cond<<<grid, BLK, 0, ctx->stream>>>(d, ctx->geo, bhat, kappa, FS);
-  k_assemble_cond_fast<<<grid, BLK, 0, ctx->stream>>>(d, ctx->geo, FS, ctx->invW, ctx->coef,
-                                                     ctx->d_lammax, ctx->d_flag);
+  if (flags & RKL_FLUX_FORM)
+    k_assemble_cond_fast<1><<<grid, BLK, 0, ctx->stream>>>(d, ctx->geo, FS, ctx->invW, ctx->coef,
+                                                          ctx->d_lammax, ctx->d_flag);
+  else
+    k_assemble_cond_fast<0><<<grid, BLK, 0, ctx->stream>>>(d, ctx->geo, FS, ctx->invW, ctx->coef,
+                                                          ctx->d_lammax, ctx->d_flag);
   ctx->launches += 3;
   return cuda_check(ctx, cudaGetLastError(), "set_coeffs(conduction) launch");
 }
@@ -341,7 +360,7 @@ int launch_setup_conduction_raw(const Dims &d, const Geo &g, cudaStream_t stream
   unsigned grid = grid_for(d.N, BLK);
   k_cell_cond<<<grid, BLK, 0, stream>>>(d, g, T, bhat, n, kappa0, flags, kappa, W, invW, flag);
   k_faces_cond<<<grid, BLK, 0, stream>>>(d, g, bhat, kappa, FS);
-  k_assemble_cond_fast<<<grid, BLK, 0, stream>>>(d, g, FS, invW, coef, lammax, flag);
+  k_assemble_cond_fast<0><<<grid, BLK, 0, stream>>>(d, g, FS, invW, coef, lammax, flag);
   return cudaGetLastError() == cudaSuccess ? RKL_OK : RKL_ECUDA;
 }
 

@@ -13,6 +13,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/rklpcg.h"
@@ -35,7 +36,24 @@ __host__ __device__ constexpr int fwd_dj(int m) {
 }
 __host__ __device__ constexpr int fwd_dk(int m) { return (m == 2 || m >= 5) ? 1 : 0; }
 
-enum { NCOEF_COND = 10, NCOEF_VISC = 4 };
+enum { NCOEF_COND = 10, NCOEF_VISC = 4, NCOEF_FULL = 19 };
+
+// Operator kinds of a context (template argument OP of the kernels): the two public
+// operators with symmetric storage, and conduction in the non-symmetric flux form
+// (RKL_FLUX_FORM) with full-row storage.
+enum { OPK_COND = RKL_OP_CONDUCTION, OPK_VISC = RKL_OP_VISCOSITY, OPK_FLUX = 2 };
+
+__host__ __device__ constexpr int op_ncoef(int op) {
+  return op == OPK_VISC ? NCOEF_VISC : (op == OPK_FLUX ? NCOEF_FULL : NCOEF_COND);
+}
+
+// f(std::integral_constant<int, OP>{}) for the operator kind op of a context
+template <typename F>
+inline void op_dispatch(int op, F &&f) {
+  if (op == OPK_COND) f(std::integral_constant<int, OPK_COND>{});
+  else if (op == OPK_FLUX) f(std::integral_constant<int, OPK_FLUX>{});
+  else f(std::integral_constant<int, OPK_VISC>{});
+}
 
 struct Dims {
   int nr, nth, nph;
@@ -108,9 +126,10 @@ struct rkl_ctx {
   rkl::Geo geo;
 
   // frozen operator
-  int op = -1;  // RKL_OP_* once set_coeffs succeeded
+  int op = -1;  // operator kind (OPK_*) once set_coeffs succeeded
   double dt_exp = 0.0;
-  double *coef = nullptr;   // NCOEF_COND * N (also used for viscosity)
+  double *coef = nullptr;   // coef_slots * N (NCOEF_COND at create, NCOEF_FULL for the flux form)
+  int coef_slots = 0;
   double *W = nullptr;      // N
   double *invW = nullptr;   // N
   double *scratch = nullptr;  // 10 * N: kappa/mu + face scalars during set_coeffs
@@ -124,6 +143,7 @@ struct rkl_ctx {
   // work fields
   int prec = RKL_F64;
   float *coef32 = nullptr, *W32 = nullptr, *invW32 = nullptr;
+  int coef32_slots = 0;
   float *M0f = nullptr, *da32 = nullptr, *db32 = nullptr;
   float *r32 = nullptr, *p32 = nullptr, *y32 = nullptr, *z32 = nullptr, *e32 = nullptr,
         *dinv32 = nullptr;

@@ -324,7 +324,7 @@ __global__ void __launch_bounds__(GB) k_bilu_factor(Dims d, IluPlan pl,
   const int gcount = min(pl.G, pl.nblocks - b0);
   const size_t gs = (size_t)pl.G * pl.bs;
   double *LUg = LU + (size_t)grp * ILU_SLOTS * gs;
-  const int nf = OP == RKL_OP_CONDUCTION ? 9 : 3;
+  const int nf = OP == RKL_OP_VISCOSITY ? 3 : 9;
   for (int lev = 0; lev < pl.nlev; lev++) {
     const int ls = pl.lev_start[lev], nl = pl.lev_start[lev + 1] - ls;
     for (int q = threadIdx.x; q < gcount * nl; q += GB) {
@@ -339,7 +339,8 @@ __global__ void __launch_bounds__(GB) k_bilu_factor(Dims d, IluPlan pl,
         if (m >= nf) continue;
         long long off = fwd_di(m) + (long long)fwd_dj(m) * d.nr + (long long)fwd_dk(m) * d.nrt;
         if (in_pattern<OP>(pl, b, 10 + m)) a[10 + m] = dt * coef[m * d.N + b.c];
-        if (in_pattern<OP>(pl, b, 1 + m)) a[1 + m] = dt * coef[m * d.N + b.c - off];
+        if (in_pattern<OP>(pl, b, 1 + m))  // full rows keep the backward entries themselves
+          a[1 + m] = dt * (OP == OPK_FLUX ? coef[(10 + m) * d.N + b.c] : coef[m * d.N + b.c - off]);
       }
       // lower slots in increasing order of the neighbour's position (lexicographic)
       for (int rk = 0; rk < 13; rk++) {
@@ -374,6 +375,9 @@ __global__ void __launch_bounds__(GB) k_bilu_factor(Dims d, IluPlan pl,
 // so their latency overlaps the current wavefront.  Per-position data (local index,
 // pattern mask, offset in the grid) is tabulated once per CTA in shared memory.
 constexpr int AB = 384;
+// the solve depends only on the pattern kept by the factorisation: the flux form keeps
+// the 19-point pattern of symmetric conduction
+constexpr int ilu_op(int op) { return op == OPK_FLUX ? OPK_COND : op; }
 constexpr int ILU_TAB_BYTES = 8192 * 8 + 4096 * 4 * 2 + 64 * 8;  // zs + tab + goff + base
 
 template <int OP, typename T>
@@ -618,10 +622,10 @@ int bilu0_prepare(rkl_ctx *ctx, const int *block, double dt) {
   }
   const unsigned int ngrp = (unsigned int)ctx->plan.ngroups;
   ProfScope prof(ctx, RKL_K_BILU_FACTOR);
-  if (ctx->op == RKL_OP_CONDUCTION)
-    k_bilu_factor<RKL_OP_CONDUCTION><<<ngrp, GB, 0, ctx->stream>>>(d, ctx->plan, ctx->coef, ctx->W, dt, ctx->LU);
-  else
-    k_bilu_factor<RKL_OP_VISCOSITY><<<ngrp, GB, 0, ctx->stream>>>(d, ctx->plan, ctx->coef, ctx->W, dt, ctx->LU);
+  op_dispatch(ctx->op, [&](auto kind) {
+    constexpr int OP = decltype(kind)::value;
+      k_bilu_factor<OP><<<ngrp, GB, 0, ctx->stream>>>(d, ctx->plan, ctx->coef, ctx->W, dt, ctx->LU);
+  });
   ctx->launches += 1;
   rc = cuda_check(ctx, cudaGetLastError(), "block-ILU0 factor launch");
   if (rc) return rc;
@@ -682,7 +686,7 @@ static void pcg_first(rkl_ctx *ctx, const PcgFields<T> &f, int pc) {
     k_jacobi_init<T><<<g, RB, 0, ctx->stream>>>(d.N, f.r, f.dinv, f.p, ctx->partials, ctx->counter, ctx->d_state);
     ctx->launches += 1;
   } else {
-    k_bilu_apply<OP, T><<<(unsigned)ctx->plan.ngroups, AB, ilu_smem(ctx, sizeof(T)), ctx->stream>>>(
+    k_bilu_apply<ilu_op(OP), T><<<(unsigned)ctx->plan.ngroups, AB, ilu_smem(ctx, sizeof(T)), ctx->stream>>>(
         d, ctx->plan, f.LU, f.r, f.z, ctx->partials, ctx->counter, ctx->d_state, 1);
     k_pupdate_z<T><<<g, RB, 0, ctx->stream>>>(d.N, f.z, f.p, ctx->d_state, 1);
     ctx->launches += 2;
@@ -728,7 +732,7 @@ static int pcg_loop(rkl_ctx *ctx, const PcgFields<T> &f, double dt, int pc, int 
         }
         {
           ProfScope prof(ctx, RKL_K_BILU_APPLY, q);
-          k_bilu_apply<OP, T><<<nblk, AB, smem, ctx->stream>>>(d, ctx->plan, f.LU, f.r, f.z, ctx->partials,
+          k_bilu_apply<ilu_op(OP), T><<<nblk, AB, smem, ctx->stream>>>(d, ctx->plan, f.LU, f.r, f.z, ctx->partials,
                                                                ctx->counter, ctx->d_state, 0);
         }
         ProfScope prof(ctx, RKL_K_PCG_PUPDATE, q);
@@ -868,13 +872,17 @@ static int pcg_run_mixed(rkl_ctx *ctx, double *x, const double *u, const double 
 int pcg_solve_component(rkl_ctx *ctx, double *x, const double *u, const double *x0, double dt,
                         int pc, double rtol, int maxit, int *iters, double *relres, int *status) {
   if (ctx->prec == RKL_F32MIX) {
-    if (ctx->op == RKL_OP_CONDUCTION)
-      return pcg_run_mixed<RKL_OP_CONDUCTION>(ctx, x, u, x0, dt, pc, rtol, maxit, iters, relres, status);
-    return pcg_run_mixed<RKL_OP_VISCOSITY>(ctx, x, u, x0, dt, pc, rtol, maxit, iters, relres, status);
+    int rc = RKL_OK;
+    op_dispatch(ctx->op, [&](auto kind) {
+      rc = pcg_run_mixed<decltype(kind)::value>(ctx, x, u, x0, dt, pc, rtol, maxit, iters, relres, status);
+    });
+    return rc;
   }
-  if (ctx->op == RKL_OP_CONDUCTION)
-    return pcg_run<RKL_OP_CONDUCTION>(ctx, x, u, x0, dt, pc, rtol, maxit, iters, relres, status);
-  return pcg_run<RKL_OP_VISCOSITY>(ctx, x, u, x0, dt, pc, rtol, maxit, iters, relres, status);
+  int rc = RKL_OK;
+  op_dispatch(ctx->op, [&](auto kind) {
+    rc = pcg_run<decltype(kind)::value>(ctx, x, u, x0, dt, pc, rtol, maxit, iters, relres, status);
+  });
+  return rc;
 }
 
 }  // namespace rkl

@@ -139,10 +139,10 @@ int launch_to_float(rkl_ctx *ctx, const double *a, float *b, long long n) {
 int launch_rkl2_first_mix(rkl_ctx *ctx, const double *Y0, float *M0f, float *d1, double mut1dt) {
   ProfScope prof(ctx, RKL_K_RKL2_FIRST);
   unsigned grid = grid_for(ctx->d.N, BLK);
-  if (ctx->op == RKL_OP_CONDUCTION)
-    k_rkl2_first_mix<RKL_OP_CONDUCTION><<<grid, BLK, 0, ctx->stream>>>(ctx->d, ctx->coef, ctx->invW, Y0, M0f, d1, mut1dt);
-  else
-    k_rkl2_first_mix<RKL_OP_VISCOSITY><<<grid, BLK, 0, ctx->stream>>>(ctx->d, ctx->coef, ctx->invW, Y0, M0f, d1, mut1dt);
+  op_dispatch(ctx->op, [&](auto kind) {
+    constexpr int OP = decltype(kind)::value;
+      k_rkl2_first_mix<OP><<<grid, BLK, 0, ctx->stream>>>(ctx->d, ctx->coef, ctx->invW, Y0, M0f, d1, mut1dt);
+  });
   ctx->launches += 1;
   return cuda_check(ctx, cudaGetLastError(), "mixed rkl2 stage-1 launch");
 }
@@ -153,12 +153,11 @@ int launch_rkl2_stage_mix(rkl_ctx *ctx, const float *dm1, const float *dm2, cons
   // a block of 256 threads: the whole (padded) r line when it is short, several theta rows
   const unsigned bx = (unsigned)std::min(256, ((ctx->d.nr + 31) / 32) * 32), by = 256 / bx;
   const dim3 block(bx, by), grid(grid_for(ctx->d.nr, bx), grid_for(ctx->d.nth, by), (unsigned)ctx->d.nph);
-  if (ctx->op == RKL_OP_CONDUCTION)
-    k_rkl2_stage_mix<RKL_OP_CONDUCTION><<<grid, block, 0, ctx->stream>>>(
-        ctx->d, ctx->coef32, ctx->invW32, dm1, dm2, M0f, dout, u, (float)mu, (float)nu, (float)mutdt, (float)cm0);
-  else
-    k_rkl2_stage_mix<RKL_OP_VISCOSITY><<<grid, block, 0, ctx->stream>>>(
-        ctx->d, ctx->coef32, ctx->invW32, dm1, dm2, M0f, dout, u, (float)mu, (float)nu, (float)mutdt, (float)cm0);
+  op_dispatch(ctx->op, [&](auto kind) {
+    constexpr int OP = decltype(kind)::value;
+      k_rkl2_stage_mix<OP><<<grid, block, 0, ctx->stream>>>(
+          ctx->d, ctx->coef32, ctx->invW32, dm1, dm2, M0f, dout, u, (float)mu, (float)nu, (float)mutdt, (float)cm0);
+  });
   ctx->launches += 1;
   return cuda_check(ctx, cudaGetLastError(), "mixed rkl2 stage launch");
 }
@@ -166,10 +165,10 @@ int launch_rkl2_stage_mix(rkl_ctx *ctx, const float *dm1, const float *dm2, cons
 int launch_apply_F(rkl_ctx *ctx, const double *u, double *Fu) {
   ProfScope prof(ctx, RKL_K_APPLY_F);
   unsigned grid = grid_for(ctx->d.N, BLK);
-  if (ctx->op == RKL_OP_CONDUCTION)
-    k_apply_F<RKL_OP_CONDUCTION><<<grid, BLK, 0, ctx->stream>>>(ctx->d, ctx->coef, ctx->invW, u, Fu);
-  else
-    k_apply_F<RKL_OP_VISCOSITY><<<grid, BLK, 0, ctx->stream>>>(ctx->d, ctx->coef, ctx->invW, u, Fu);
+  op_dispatch(ctx->op, [&](auto kind) {
+    constexpr int OP = decltype(kind)::value;
+      k_apply_F<OP><<<grid, BLK, 0, ctx->stream>>>(ctx->d, ctx->coef, ctx->invW, u, Fu);
+  });
   ctx->launches += 1;
   return cuda_check(ctx, cudaGetLastError(), "apply_F launch");
 }
@@ -177,12 +176,11 @@ int launch_apply_F(rkl_ctx *ctx, const double *u, double *Fu) {
 int launch_rkl2_stage1(rkl_ctx *ctx, const double *Y0, double *M0, double *Y1, double mut1dt) {
   ProfScope prof(ctx, RKL_K_RKL2_FIRST);
   unsigned grid = grid_for(ctx->d.N, BLK);
-  if (ctx->op == RKL_OP_CONDUCTION)
-    k_rkl2_first<RKL_OP_CONDUCTION><<<grid, BLK, 0, ctx->stream>>>(ctx->d, ctx->coef, ctx->invW, Y0, M0,
-                                                              Y1, mut1dt);
-  else
-    k_rkl2_first<RKL_OP_VISCOSITY><<<grid, BLK, 0, ctx->stream>>>(ctx->d, ctx->coef, ctx->invW, Y0, M0,
-                                                             Y1, mut1dt);
+  op_dispatch(ctx->op, [&](auto kind) {
+    constexpr int OP = decltype(kind)::value;
+      k_rkl2_first<OP><<<grid, BLK, 0, ctx->stream>>>(ctx->d, ctx->coef, ctx->invW, Y0, M0,
+                                                                Y1, mut1dt);
+  });
   ctx->launches += 1;
   return cuda_check(ctx, cudaGetLastError(), "rkl2 stage-1 launch");
 }
@@ -193,14 +191,12 @@ int launch_rkl2_stage(rkl_ctx *ctx, const double *Ym1, const double *Ym2, const 
   ProfScope prof(ctx, RKL_K_RKL2_STAGE);
   unsigned grid = grid_for(ctx->d.N, BLK);
   double om = 1.0 - mu - nu;
-  if (ctx->op == RKL_OP_CONDUCTION)
-    k_rkl2_stage<RKL_OP_CONDUCTION><<<grid, BLK, 0, ctx->stream>>>(ctx->d, ctx->coef, ctx->invW, Ym1,
-                                                             Ym2, Y0, M0, Yout, mu, nu, om, mutdt,
-                                                             gtdt);
-  else
-    k_rkl2_stage<RKL_OP_VISCOSITY><<<grid, BLK, 0, ctx->stream>>>(ctx->d, ctx->coef, ctx->invW, Ym1,
-                                                            Ym2, Y0, M0, Yout, mu, nu, om, mutdt,
-                                                            gtdt);
+  op_dispatch(ctx->op, [&](auto kind) {
+    constexpr int OP = decltype(kind)::value;
+      k_rkl2_stage<OP><<<grid, BLK, 0, ctx->stream>>>(ctx->d, ctx->coef, ctx->invW, Ym1,
+                                                               Ym2, Y0, M0, Yout, mu, nu, om, mutdt,
+                                                               gtdt);
+  });
   ctx->launches += 1;
   return cuda_check(ctx, cudaGetLastError(), "rkl2 stage launch");
 }

@@ -79,16 +79,39 @@ __device__ __forceinline__ T S_apply_visc(const Dims &d, const T *__restrict__ c
   return acc;
 }
 
+// 19-point operator stored as full rows, coef = [19][N]: slot m < 9 the entry towards
+// c + FWD[m], slot 9 the diagonal, slot 10 + m the entry towards c - FWD[m] (zero for a
+// missing neighbour, whose index is clamped onto a valid cell).  Used for the
+// non-symmetric flux form of conduction.
+template <typename T>
+__device__ __forceinline__ T S_apply_full(const Dims &d, const T *__restrict__ coef,
+                                          const T *__restrict__ u, long long c, const Nbr &n) {
+  const long long N = d.N;
+  const long long f[9] = {c + n.rp,        c + n.tp,        c + n.pp,
+                          c + n.rm + n.tp, c + n.rp + n.tp, c + n.rm + n.pp,
+                          c + n.rp + n.pp, c + n.tm + n.pp, c + n.tp + n.pp};
+  const long long b[9] = {c + n.rm,        c + n.tm,        c + n.pm,
+                          c + n.rp + n.tm, c + n.rm + n.tm, c + n.rp + n.pm,
+                          c + n.rm + n.pm, c + n.tp + n.pm, c + n.tm + n.pm};
+  T acc = coef[9 * N + c] * u[c];
+#pragma unroll
+  for (int m = 0; m < 9; m++) acc = fma(coef[m * N + c], u[f[m]], acc);
+#pragma unroll
+  for (int m = 0; m < 9; m++) acc = fma(coef[(10 + m) * N + c], u[b[m]], acc);
+  return acc;
+}
+
 template <int OP, typename T>
 __device__ __forceinline__ T S_apply(const Dims &d, const T *__restrict__ coef,
                                      const T *__restrict__ u, long long c, const Nbr &n) {
   if (OP == RKL_OP_CONDUCTION) return S_apply_cond<T>(d, coef, u, c, n);
+  if (OP == OPK_FLUX) return S_apply_full<T>(d, coef, u, c, n);
   return S_apply_visc<T>(d, coef, u, c, n);
 }
 
 template <int OP, typename T>
 __device__ __forceinline__ T S_diag(const Dims &d, const T *__restrict__ coef, long long c) {
-  return coef[(OP == RKL_OP_CONDUCTION ? 9 : 3) * d.N + c];
+  return coef[(OP == RKL_OP_VISCOSITY ? 3 : 9) * d.N + c];
 }
 
 }  // namespace rkl
