@@ -50,11 +50,12 @@ FP64_PEAK_TFLOPS = 1.25  # nominal FP64 rate of the GB300 (2 DFMA/clk/SM x 152 S
 #  bilu_apply cond: 9 + 9 FMA + 1/U_ii + r.z, r.r = 41 flop; 19 factors + r + z = 168 B
 #  bilu_apply visc: 3 + 3 FMA + 1 + 4 = 17 flop; 7 factors + r + z = 72 B
 KERNEL_COST = {
-    ("conduction", "rkl2_stage"): (48.0, 128.0, "alu", "rkl2_stage_128x192x384.md", ("rkl2.cu", "stencil.cuh")),
+    ("conduction", "rkl2_stage"): (48.0, 128.0, "alu", "rkl2_stage_128x192x384.md",
+                                   ("rkl2.cu:k_rkl2_stage", "stencil.cuh")),
     ("viscosity", "rkl2_stage"): (24.0, 80.0, "alu", None, ()),
-    ("conduction", "spmv"): (43.0, 104.0, "alu", "spmv_128x192x384.md", ("pcg.cu", "stencil.cuh")),
+    ("conduction", "spmv"): (43.0, 104.0, "alu", "spmv_128x192x384.md", ("pcg.cu:k_spmv", "stencil.cuh")),
     ("viscosity", "spmv"): (19.0, 56.0, "alu", None, ()),
-    ("conduction", "bilu_apply"): (41.0, 168.0, "alu", "bilu_apply_128x192x384.md", ("pcg.cu",)),
+    ("conduction", "bilu_apply"): (41.0, 168.0, "alu", "bilu_apply_128x192x384.md", ("pcg.cu:k_bilu_apply",)),
     ("viscosity", "bilu_apply"): (17.0, 72.0, "alu", None, ()),
 }
 WORKLOAD = "coronal FP64 conduction+viscosity, 128x192x384 spherical grid"
@@ -220,11 +221,35 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def kernel_source_hash(names=("rkl2.cu", "stencil.cuh")):
+def _function_text(text, func):
+    """Source of the __global__ function `func` (with its template line), or the whole text."""
+    m = re.search(r"__global__[^;{]*?\b" + re.escape(func) + r"\s*\(", text)
+    if not m:
+        return text
+    start = text.rfind("\n", 0, m.start()) + 1
+    prev = text.rfind("\n", 0, start - 1) + 1
+    if text[prev:start].lstrip().startswith("template"):
+        start = prev
+    depth, pos = 0, text.index("{", m.end())
+    for q in range(pos, len(text)):
+        if text[q] == "{":
+            depth += 1
+        elif text[q] == "}":
+            depth -= 1
+            if depth == 0:
+                return text[start:q + 1]
+    return text[start:]
+
+
+def kernel_source_hash(names=("rkl2.cu:k_rkl2_stage", "stencil.cuh")):
+    """Hash of the source a kernel is built from: 'file:function' hashes that function's
+    text, 'file' the whole file (headers the kernel includes)."""
     h = hashlib.sha256()
     for name in names:
-        with open(os.path.join(ROOT, "paper_1610_01265_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
+        fname, _, func = name.partition(":")
+        with open(os.path.join(ROOT, "paper_1610_01265_gb300", "csrc", fname)) as f:
+            text = f.read()
+        h.update((_function_text(text, func) if func else text).encode())
     return h.hexdigest()[:16]
 
 
