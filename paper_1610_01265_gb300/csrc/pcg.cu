@@ -33,10 +33,12 @@ __device__ __forceinline__ int slot_dj(int s) { return s == 0 ? 0 : (s < 10 ? -f
 __device__ __forceinline__ int slot_dk(int s) { return s == 0 ? 0 : (s < 10 ? -fwd_dk(s - 1) : fwd_dk(s - 10)); }
 
 // Sum NV per-thread values over the whole grid.  Returns true (in every thread of the
-// last block to finish) with the totals in tot[] of thread 0.
+// last block to finish) with the totals in tot[] of thread 0.  Blocks must be 1-D with
+// exactly BS threads (threadIdx.x is the thread's rank; one counter increment per block);
+// bid / nb are the block's linear index and the number of blocks.
 template <int NV, int BS>
 __device__ bool grid_sum(double (&v)[NV], double *partials, unsigned int *counter,
-                         double (&tot)[NV]) {
+                         double (&tot)[NV], unsigned int bid, unsigned int nb) {
   __shared__ double sh[NV][BS / 32];
   __shared__ bool last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -52,11 +54,11 @@ __device__ bool grid_sum(double (&v)[NV], double *partials, unsigned int *counte
     for (int q = 0; q < NV; q++) {
       double s = 0.0;
       for (int w = 0; w < BS / 32; w++) s += sh[q][w];
-      partials[(size_t)blockIdx.x * NV + q] = s;
+      partials[(size_t)bid * NV + q] = s;
     }
     __threadfence();
     unsigned int t = atomicAdd(counter, 1u);
-    last = (t == gridDim.x - 1);
+    last = (t == nb - 1);
   }
   __syncthreads();
   if (!last) return false;
@@ -64,7 +66,7 @@ __device__ bool grid_sum(double (&v)[NV], double *partials, unsigned int *counte
 #pragma unroll
   for (int q = 0; q < NV; q++) {
     double s = 0.0;
-    for (unsigned int b = threadIdx.x; b < gridDim.x; b += BS) s += __ldcg(&partials[(size_t)b * NV + q]);
+    for (unsigned int b = threadIdx.x; b < nb; b += BS) s += __ldcg(&partials[(size_t)b * NV + q]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
     if (lane == 0) sh[q][warp] = s;
@@ -80,6 +82,11 @@ __device__ bool grid_sum(double (&v)[NV], double *partials, unsigned int *counte
     *counter = 0u;
   }
   return true;
+}
+
+template <int NV, int BS>
+__device__ bool grid_sum(double (&v)[NV], double *partials, unsigned int *counter, double (&tot)[NV]) {
+  return grid_sum<NV, BS>(v, partials, counter, tot, blockIdx.x, gridDim.x);
 }
 
 // r.z and r.r after a preconditioner application: the convergence test of Fig. 1
@@ -170,6 +177,107 @@ __global__ void __launch_bounds__(RB) k_spmv(Dims d, const T *__restrict__ coef,
   }
   double tot[1];
   if (grid_sum<1, RB>(v, partials, counter, tot) && threadIdx.x == 0) {
+    double pAp = tot[0];
+    st->pAp = pAp;
+    if (!(pAp > 0.0) || !isfinite(pAp)) st->status = PCG_BREAKDOWN;
+    else st->alpha = st->rr / pAp;
+  }
+}
+
+// FP32 y = A p for the symmetric 19-point conduction operator, marching along phi like
+// k_rkl2_stage_mix_march (rkl2.cu): a CTA owns a 32 x 8 (r, theta) tile and a chunk of
+// phi planes, one thread per cell of the tile and its halo stages p and the
+// coefficients once per plane in shared memory.  Same sums, same order as k_spmv per
+// cell; p.y is accumulated per thread over its planes, then reduced over the grid.
+constexpr int MR = 32, MT = 8, MHR = MR + 2, MHT = MT + 2, MPL = MHR * MHT;
+constexpr int MTHREADS = 352;
+
+__global__ void __launch_bounds__(MTHREADS) k_spmv_march(Dims d, const float *__restrict__ coef,
+                                                         const float *__restrict__ W, float dt,
+                                                         const float *__restrict__ p, float *__restrict__ y,
+                                                         double *partials, unsigned int *counter, PcgState *st,
+                                                         int kchunk) {
+  if (st->status != PCG_RUNNING) return;
+  __shared__ float sd[3][MPL];
+  __shared__ float sc[4][MPL];
+  __shared__ float sp[2][5][MPL];
+  const int t = threadIdx.x;
+  const bool active = t < MPL;
+  const int tx = t % MHR, ty = t / MHR;
+  const int i = blockIdx.x * MR + tx - 1, j = blockIdx.y * MT + ty - 1;
+  const bool inside = active && i >= 0 && i < d.nr && j >= 0 && j < d.nth;
+  const bool interior = inside && tx >= 1 && tx <= MR && ty >= 1 && ty <= MT;
+  const long long col = inside ? (long long)j * d.nr + i : 0;
+  const long long N = d.N;
+  const int k0 = blockIdx.z * kchunk, k1 = min(k0 + kchunk, d.nph);
+  auto wrap = [&](int k) { return k < 0 ? k + d.nph : (k >= d.nph ? k - d.nph : k); };
+  auto cell = [&](int k) { return (long long)wrap(k) * d.nrt + col; };
+  auto rs = [&](int k) { return (k - k0 + 1) % 3; };
+  const int fw[4] = {0, 1, 3, 4}, bw[5] = {2, 5, 6, 7, 8};
+  double v[1] = {0.0};
+  float nf[10], nd = 0.0f, nw = 0.0f;  // next plane's loads, issued one plane ahead
+  auto fetch = [&](int k) {
+    const long long c = cell(k);
+#pragma unroll
+    for (int m = 0; m < 10; m++) nf[m] = inside ? coef[m * N + c] : 0.0f;
+    nd = inside ? p[cell(k + 1)] : 0.0f;
+    if (interior) nw = W[c];
+  };
+  if (active) {
+    const long long cm = cell(k0 - 1);
+    sd[rs(k0 - 1)][t] = inside ? p[cm] : 0.0f;
+    sd[rs(k0)][t] = inside ? p[cell(k0)] : 0.0f;
+#pragma unroll
+    for (int q = 0; q < 5; q++) sp[(k0 + 1) & 1][q][t] = inside ? coef[bw[q] * N + cm] : 0.0f;
+    fetch(k0);
+  }
+  for (int k = k0; k < k1; k++) {
+    float cf[10];
+    const float wc = nw;
+    if (active) {
+#pragma unroll
+      for (int m = 0; m < 10; m++) cf[m] = nf[m];
+      sd[rs(k + 1)][t] = nd;
+#pragma unroll
+      for (int q = 0; q < 4; q++) sc[q][t] = cf[fw[q]];
+#pragma unroll
+      for (int q = 0; q < 5; q++) sp[k & 1][q][t] = cf[bw[q]];
+    }
+    __syncthreads();
+    if (active && k + 1 < k1) fetch(k + 1);
+    if (interior) {
+      const float *D0 = sd[rs(k)], *Dp = sd[rs(k + 1)], *Dm = sd[rs(k - 1)];
+      const float(*P)[MPL] = sp[(k + 1) & 1];
+      float acc = cf[9] * D0[t];
+      acc = fmaf(cf[0], D0[t + 1], acc);
+      acc = fmaf(cf[1], D0[t + MHR], acc);
+      acc = fmaf(cf[2], Dp[t], acc);
+      acc = fmaf(cf[3], D0[t - 1 + MHR], acc);
+      acc = fmaf(cf[4], D0[t + 1 + MHR], acc);
+      acc = fmaf(cf[5], Dp[t - 1], acc);
+      acc = fmaf(cf[6], Dp[t + 1], acc);
+      acc = fmaf(cf[7], Dp[t - MHR], acc);
+      acc = fmaf(cf[8], Dp[t + MHR], acc);
+      acc = fmaf(sc[0][t - 1], D0[t - 1], acc);
+      acc = fmaf(sc[1][t - MHR], D0[t - MHR], acc);
+      acc = fmaf(P[0][t], Dm[t], acc);
+      acc = fmaf(sc[2][t + 1 - MHR], D0[t + 1 - MHR], acc);
+      acc = fmaf(sc[3][t - 1 - MHR], D0[t - 1 - MHR], acc);
+      acc = fmaf(P[1][t + 1], Dm[t + 1], acc);
+      acc = fmaf(P[2][t - 1], Dm[t - 1], acc);
+      acc = fmaf(P[3][t + MHR], Dm[t + MHR], acc);
+      acc = fmaf(P[4][t - MHR], Dm[t - MHR], acc);
+      const float pc = D0[t];
+      const float yv = fmaf(wc, pc, dt * acc);
+      y[cell(k)] = yv;
+      v[0] = fma((double)pc, (double)yv, v[0]);
+    }
+    __syncthreads();
+  }
+  double tot[1];
+  const unsigned int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+  const unsigned int nb = gridDim.x * gridDim.y * gridDim.z;
+  if (grid_sum<1, MTHREADS>(v, partials, counter, tot, bid, nb) && threadIdx.x == 0) {
     double pAp = tot[0];
     st->pAp = pAp;
     if (!(pAp > 0.0) || !isfinite(pAp)) st->status = PCG_BREAKDOWN;
@@ -378,7 +486,10 @@ constexpr int AB = 384;
 // the solve depends only on the pattern kept by the factorisation: the flux form keeps
 // the 19-point pattern of symmetric conduction
 constexpr int ilu_op(int op) { return op == OPK_FLUX ? OPK_COND : op; }
-constexpr int ILU_TAB_BYTES = 8192 * 8 + 4096 * 4 * 2 + 64 * 8;  // zs + tab + goff + base
+constexpr int ILU_TAB_BYTES = (8192 + 64) * 8 + 4096 * 4 * 2 + 64 * 8;  // zs + tab + goff + base
+// per-block stride of the staged residual: odd, so that the same local cell of the G
+// blocks of a group falls into different shared-memory banks
+__host__ __device__ constexpr int ilu_zstride(int bs) { return bs | 1; }
 
 template <int OP, typename T>
 __global__ void __launch_bounds__(AB) k_bilu_apply(Dims d, IluPlan pl,
@@ -390,8 +501,9 @@ __global__ void __launch_bounds__(AB) k_bilu_apply(Dims d, IluPlan pl,
   if (!init && st->status != PCG_RUNNING) return;
   extern __shared__ double smem[];
   const int bs = pl.bs;
-  T *zs = reinterpret_cast<T *>(smem);                      // [G][bs] by local index
-  long long *base = (long long *)(smem + ((size_t)pl.G * bs * sizeof(T) + 7) / 8);  // [G]
+  const int zst = ilu_zstride(bs);
+  T *zs = reinterpret_cast<T *>(smem);                      // [G][zst] by local index
+  long long *base = (long long *)(smem + ((size_t)pl.G * zst * sizeof(T) + 7) / 8);  // [G]
   int *tab = (int *)(base + pl.G);                          // [bs] level order: l | mask << 12
   int *goff = tab + bs;                                     // [bs] by local index
   const int grp = blockIdx.x, b0 = grp * pl.G;
@@ -421,7 +533,7 @@ __global__ void __launch_bounds__(AB) k_bilu_apply(Dims d, IluPlan pl,
   __syncthreads();
   for (int q = tid; q < gcount * bs; q += AB) {
     const int bb = q / bs;
-    zs[q] = r[base[bb] + goff[q - bb * bs]];
+    zs[bb * zst + (q - bb * bs)] = r[base[bb] + goff[q - bb * bs]];
   }
   int dl[NSL];  // local-index offset of every slot
 #pragma unroll
@@ -453,7 +565,7 @@ __global__ void __launch_bounds__(AB) k_bilu_apply(Dims d, IluPlan pl,
     for (int q = tid; q < gcount * nl; q += AB) {
       const int bb = q / nl;
       const int t = tab[ls + (q - bb * nl)], l = t & 0xfff, mask = t >> 12;
-      T *zb = zs + bb * bs;
+      T *zb = zs + bb * zst;
       T v = zb[l];
       if (q == tid) {
 #pragma unroll
@@ -496,7 +608,7 @@ __global__ void __launch_bounds__(AB) k_bilu_apply(Dims d, IluPlan pl,
     for (int q = tid; q < gcount * nl; q += AB) {
       const int bb = q / nl;
       const int t = tab[ls + (q - bb * nl)], l = t & 0xfff, mask = t >> 12;
-      T *zb = zs + bb * bs;
+      T *zb = zs + bb * zst;
       T v = zb[l];
       if (q == tid) {
 #pragma unroll
@@ -517,7 +629,7 @@ __global__ void __launch_bounds__(AB) k_bilu_apply(Dims d, IluPlan pl,
   for (int q = tid; q < gcount * bs; q += AB) {
     const int bb = q / bs;
     const long long c = base[bb] + goff[q - bb * bs];
-    const T zv = zs[q], rv = r[c];
+    const T zv = zs[bb * zst + (q - bb * bs)], rv = r[c];
     z[c] = zv;
     v2[0] = fma((double)rv, (double)zv, v2[0]);
     v2[1] = fma((double)rv, (double)rv, v2[1]);
@@ -673,7 +785,7 @@ static int state_read(rkl_ctx *ctx) {
 
 static size_t ilu_smem(const rkl_ctx *ctx, size_t elem) {
   const IluPlan &pl = ctx->plan;
-  return ((elem * pl.G * pl.bs + 7) / 8) * 8 + sizeof(long long) * pl.G + 2 * sizeof(int) * pl.bs;
+  return ((elem * pl.G * ilu_zstride(pl.bs) + 7) / 8) * 8 + sizeof(long long) * pl.G + 2 * sizeof(int) * pl.bs;
 }
 
 // first preconditioner application once r (and for PC1 the diagonal) is in place and
@@ -705,17 +817,35 @@ static int pcg_loop(rkl_ctx *ctx, const PcgFields<T> &f, double dt, int pc, int 
   const T tdt = (T)dt;
   const int chunk = 8;
   int it_prev = 0, rc;
+  // FP32 symmetric conduction: the phi-marching y = A p when its CTAs fit the partials
+  const int nbx = (d.nr + MR - 1) / MR, nby = (d.nth + MT - 1) / MT;
+  const int nz = std::max(1, std::min(d.nph, (8 * ctx->nsm + nbx * nby - 1) / (nbx * nby)));
+  const int kchunk = (d.nph + nz - 1) / nz;
+  const dim3 mgrid(nbx, nby, (d.nph + kchunk - 1) / kchunk);
+  const bool march = std::is_same<T, float>::value && OP == OPK_COND &&
+                     (long long)mgrid.x * mgrid.y * mgrid.z <= (long long)ctx->npart;
+  // host-side bound: the device counts iterations and stops at maxit; should its status
+  // ever stop advancing, the host stops queueing after maxit + 2 chunks
+  long long queued = 0;
   for (;;) {
     if ((rc = state_read(ctx))) return rc;
     const PcgState &h = *ctx->h_state;
     if (ctx->prof_on) prof_settle(ctx, h.iters - it_prev, h.status == PCG_RUNNING, true);
     it_prev = h.iters;
     if (h.status != PCG_RUNNING || h.iters >= maxit) break;
+    if (queued > (long long)maxit + 2 * chunk)
+      return set_error(ctx, RKL_ECUDA, "PCG: device iteration count is not advancing");
+    queued += chunk;
     for (int q = 0; q < chunk; q++) {
       {
         ProfScope prof(ctx, RKL_K_SPMV, q);
-        k_spmv<OP, T><<<g, RB, 0, ctx->stream>>>(d, f.coef, f.W, tdt, f.p, f.y, ctx->partials, ctx->counter,
-                                                 ctx->d_state);
+        if (march)
+          k_spmv_march<<<mgrid, MTHREADS, 0, ctx->stream>>>(d, (const float *)f.coef, (const float *)f.W, (float)dt,
+                                                           (const float *)f.p, (float *)f.y, ctx->partials,
+                                                           ctx->counter, ctx->d_state, kchunk);
+        else
+          k_spmv<OP, T><<<g, RB, 0, ctx->stream>>>(d, f.coef, f.W, tdt, f.p, f.y, ctx->partials, ctx->counter,
+                                                   ctx->d_state);
       }
       if (pc == RKL_PC_JACOBI) {
         {

@@ -33,7 +33,8 @@ def dev(a):
     return torch.from_numpy(np.array(a, dtype=np.float64)).cuda()
 
 
-@pytest.mark.parametrize("dims", [(16, 12, 24), (32, 32, 64)])
+# (37, 11, 13): ragged against the 32 x 8 tiles and the phi chunks of the marching kernels
+@pytest.mark.parametrize("dims", [(16, 12, 24), (32, 32, 64), (37, 11, 13)])
 @pytest.mark.parametrize("ratio", [100.0, 1000.0, 10000.0])
 def test_mixed_rkl2_conduction(oracle_mod, R, dims, ratio):
     O = oracle_mod
@@ -72,24 +73,28 @@ def test_mixed_rkl2_viscosity(oracle_mod, R):
     ctx.close()
 
 
-@pytest.mark.parametrize("pc", [1, 2])
-@pytest.mark.parametrize("ratio", [100.0, 10000.0])
-def test_mixed_be_meets_fp64_residual(oracle_mod, R, pc, ratio):
+# (37, 11, 13) is ragged against the tiles of the FP32 SpMV; block ILU0 on its thin
+# (37, 11, 1) blocks is a weaker preconditioner than Jacobi there (1161 vs 703 FP64
+# iterations at 1e4 dt_exp), so that case runs at 100 dt_exp
+@pytest.mark.parametrize("pc,ratio,dims", [(1, 100.0, (32, 32, 64)), (2, 100.0, (32, 32, 64)),
+                                           (1, 10000.0, (32, 32, 64)), (2, 10000.0, (32, 32, 64)),
+                                           (1, 10000.0, (37, 11, 13)), (2, 100.0, (37, 11, 13))])
+def test_mixed_be_meets_fp64_residual(oracle_mod, R, pc, ratio, dims):
     O = oracle_mod
-    dims = (32, 32, 64)
+    block = (8, 8, 8) if dims[0] % 8 == 0 else (37, 11, 1)
     c = synth.conduction_case(*dims, seed=3)
     g = O.Grid(c["rf"], dims[1], dims[2])
     S, W = O.assemble_conduction(g, c["T"], c["bhat"], c["n"])
     ctx = R.Context(c["rf"], dims[1], dims[2], prec=R.RKL_F32MIX)
     dte = ctx.set_conduction(dev(c["T"]), dev(c["bhat"]), dev(c["n"]))
     u = dev(c["T"])
-    code, its, rel = ctx.be_pcg_solve(u, ratio * dte, pc=pc, block=(8, 8, 8), rtol=1e-10, maxit=20000)
+    code, its, rel = ctx.be_pcg_solve(u, ratio * dte, pc=pc, block=block, rtol=1e-10, maxit=20000)
     assert code == R.RKL_OK and rel[0] <= 1e-10
     xg = u.cpu().numpy().reshape(g.shape)
     Wg = W.reshape(g.shape)
     res = Wg * (c["T"] - xg + ratio * dte * O.apply_F(g, S, W, xg))
     assert np.linalg.norm(res) <= 2e-10 * np.linalg.norm(Wg * c["T"])
-    x64, it64, rel64, st = O.be_pcg(g, S, W, c["T"], ratio * dte, pc=pc, block=(8, 8, 8), rtol=1e-10)
+    x64, it64, rel64, st = O.be_pcg(g, S, W, c["T"], ratio * dte, pc=pc, block=block, rtol=1e-10)
     assert its[0] <= 3 * it64 + 50  # FP32 correction solves restart CG a few times
     ctx.close()
 
