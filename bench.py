@@ -45,16 +45,17 @@ FP64_PEAK_TFLOPS = 1.25  # nominal FP64 rate of the GB300 (2 DFMA/clk/SM x 152 S
 #  rkl2_stage cond: 19 stencil FMA + 1/W scaling + 5 recurrence terms = 48 flop;
 #                   10 coefficients + 1/W + Y_{j-1}, Y_{j-2}, Y_0, M_0 read, Y_j written = 128 B
 #  rkl2_stage visc: 7 FMA + 1 + 9 = 24 flop; 4 coefficients + 1/W + 5 fields = 80 B
-#  spmv cond: 19 FMA + dt scaling + W p + p.y = 43 flop; 10 coefficients + W + p + y = 104 B
-#  spmv visc: 7 FMA + 1 + 2 + 2 = 19 flop; 4 coefficients + W + p + y = 56 B
+#  spmv cond: y = A p with A = W + dt S assembled once per solve: 19 FMA + p.y = 40 flop;
+#             10 coefficients of A + p + y = 96 B
+#  spmv visc: 7 FMA + p.y = 16 flop; 4 coefficients + p + y = 48 B
 #  bilu_apply cond: 9 + 9 FMA + 1/U_ii + r.z, r.r = 41 flop; 19 factors + r + z = 168 B
 #  bilu_apply visc: 3 + 3 FMA + 1 + 4 = 17 flop; 7 factors + r + z = 72 B
 KERNEL_COST = {
     ("conduction", "rkl2_stage"): (48.0, 128.0, "alu", "rkl2_stage_128x192x384.md",
                                    ("rkl2.cu:k_rkl2_stage", "stencil.cuh")),
     ("viscosity", "rkl2_stage"): (24.0, 80.0, "alu", None, ()),
-    ("conduction", "spmv"): (43.0, 104.0, "alu", "spmv_128x192x384.md", ("pcg.cu:k_spmv", "stencil.cuh")),
-    ("viscosity", "spmv"): (19.0, 56.0, "alu", None, ()),
+    ("conduction", "spmv"): (40.0, 96.0, "alu", "spmv_128x192x384.md", ("pcg.cu:k_spmv_a", "stencil.cuh")),
+    ("viscosity", "spmv"): (16.0, 48.0, "alu", None, ()),
     ("conduction", "bilu_apply"): (41.0, 168.0, "alu", "bilu_apply_128x192x384.md", ("pcg.cu:k_bilu_apply",)),
     ("viscosity", "bilu_apply"): (17.0, 72.0, "alu", None, ()),
 }
@@ -651,12 +652,20 @@ def mixed_large_report(seed=1, dims=MIXED_GRID, ratios=RATIOS, log=None):
             (code64, its64, _), b64 = timed(lambda: ctx64.be_pcg_solve(ref, dt, pc=pc, block=BLOCK, rtol=RTOL,
                                                                         maxit=MAXIT))
             u.copy_(T)
+            mix.profile_enable(True)
             (codem, itsm, relm), bm = timed(lambda: mix.be_pcg_solve(u, dt, pc=pc, block=BLOCK, rtol=RTOL,
                                                                      maxit=MAXIT))
+            sp_ms, sp_n = mix.profile().get("spmv", (0.0, 0))
+            mix.profile_enable(False)
             r[f"be_{name}"] = {"fp64_iters": its64[0], "fp64_ms": b64, "mixed_fp32_iters": itsm[0], "mixed_ms": bm,
                                "mixed_relres_fp64": relm[0], "converged": code64 == R.RKL_OK and codem == R.RKL_OK,
                                "err_rel_change": torch.linalg.vector_norm(u - ref).item()
                                / torch.linalg.vector_norm(ref - T).item()}
+            if sp_n:  # FP32 y = A p: 10 coefficients + W + p + y = 52 B per cell
+                t = sp_ms / sp_n * 1e-3
+                r[f"be_{name}"]["fp32_spmv_kernel"] = {
+                    "launch_ms": t * 1e3, "hbm_gbs": 52.0 * N / t / 1e9,
+                    "hbm_frac": 52.0 * N / t / 1e9 / measured_peaks().get("hbm_gbs", 6800.0)}
         out[str(int(ratio))] = r
         if log:
             log(f"ratio {ratio}: {r}")
