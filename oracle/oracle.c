@@ -161,9 +161,10 @@ static long nbr(const grid *g, int i, int j, int k, int s) {
 
 /* ---------------- coefficients (Sec. 4.1) ---------------- */
 static double kappa_of(double T, double kappa0, int beta_tcut) {
-  /* reading of beta_Tcut: the conduction coefficient is evaluated at max(T, T_cut) */
-  double Te = (beta_tcut && T < OR_TCUT) ? OR_TCUT : T;
-  return kappa0 * pow(Te, 2.5);
+  /* beta_Tcut (Sec. 4.1) as printed: kappa0 T^{5/2} times (T / T_cut)^{5/2} below T_cut */
+  double k = kappa0 * pow(T, 2.5);
+  if (beta_tcut && T < OR_TCUT) k *= pow(T / OR_TCUT, 2.5);
+  return k;
 }
 
 static void cell_tensor(const double *T, const double *bhat, long N, long c, double kappa0,

@@ -259,16 +259,19 @@ def test_gershgorin_bounds(oracle_mod):
     assert lam <= lam_g * (1 + 1e-12) and lam_g <= math.sqrt(7) * lam
 
 
-def test_beta_tcut_raises_low_temperature_conductivity(oracle_mod):
-    """beta_Tcut flag: cells below 5e5 K conduct as if at 5e5 K; others are unchanged."""
+def test_beta_tcut_factor(oracle_mod):
+    """beta_Tcut flag (Sec. 4.1, the printed factor): cells below 5e5 K have kappa0 T^{5/2}
+    multiplied by (T / 5e5)^{5/2}; others are unchanged.  With uniform T and bhat the
+    operator is linear in kappa, so the flagged operator at 2e5 K is (0.4)^{5/2} times the
+    plain one."""
     O = oracle_mod
     nr, nth, nph = 6, 4, 6
     g = O.Grid(synth.r_faces(nr), nth, nph)
     one = np.ones(g.shape)
     b = np.stack([one, 0 * one, 0 * one])
     S_lo, _ = O.assemble_conduction(g, 2e5 * one, b, one, beta_tcut=True)
-    S_cut, _ = O.assemble_conduction(g, 5e5 * one, b, one)
-    assert np.allclose(S_lo, S_cut, rtol=1e-15, atol=0)
+    S_lo0, _ = O.assemble_conduction(g, 2e5 * one, b, one)
+    assert np.allclose(S_lo, 0.4**2.5 * S_lo0, rtol=1e-14, atol=0)
     S_hi, _ = O.assemble_conduction(g, 8e5 * one, b, one, beta_tcut=True)
     S_hi0, _ = O.assemble_conduction(g, 8e5 * one, b, one)
     assert np.array_equal(S_hi, S_hi0)
