@@ -237,7 +237,8 @@ int rkl_destroy(rkl_ctx *ctx) {
   cudaStreamSynchronize(ctx->stream);
   prof_release(ctx);
   double *bufs[] = {ctx->geo_buf, ctx->coef, ctx->W, ctx->invW, ctx->scratch, ctx->M0, ctx->Ya, ctx->Yb,
-                    ctx->r, ctx->p, ctx->y, ctx->zbuf, ctx->dinv, ctx->partials, ctx->LU, ctx->stage, ctx->stage2};
+                    ctx->r, ctx->p, ctx->y, ctx->zbuf, ctx->dinv, ctx->partials, ctx->LU, ctx->stage, ctx->stage2,
+                    ctx->acoef};
   for (double *b : bufs)
     if (b) cudaFree(b);
   if (ctx->d_lammax) cudaFree(ctx->d_lammax);
@@ -275,6 +276,7 @@ int set_coeffs(rkl_ctx *ctx, int op, const double *a, const double *b, const dou
   const int kind = (op == RKL_OP_CONDUCTION && (flags & RKL_FLUX_FORM)) ? OPK_FLUX : op;
   ctx->op = -1;
   ctx->lu_valid = 0;
+  ctx->acoef_valid = 0;
   int rc = ensure_buffer(ctx, &ctx->scratch, 10 * N, "alloc set_coeffs scratch");
   if (rc) return rc;
   if (op_ncoef(kind) > ctx->coef_slots) {  // full rows need 19 slots

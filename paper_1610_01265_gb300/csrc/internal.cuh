@@ -153,6 +153,9 @@ struct rkl_ctx {
 
   // PCG
   double *r = nullptr, *p = nullptr, *y = nullptr, *zbuf = nullptr, *dinv = nullptr;
+  double *acoef = nullptr;  // A = W + dt S in the operator's storage (FP64 solves)
+  int acoef_slots = 0, acoef_valid = 0;
+  double acoef_dt = 0.0;
   double *partials = nullptr;
   int npart = 0;
   unsigned int *counter = nullptr;

@@ -184,6 +184,45 @@ __global__ void __launch_bounds__(RB) k_spmv(Dims d, const T *__restrict__ coef,
   }
 }
 
+// A = W + dt S in the storage of S (off-diagonal slots dt S, diagonal slot W + dt S_cc),
+// built once per FP64 solve so that an iteration's y = A p is the stencil alone (19 FP64
+// instructions per conduction row instead of 21)
+template <int OP>
+__global__ void __launch_bounds__(RB) k_assemble_A(Dims d, const double *__restrict__ coef,
+                                                   const double *__restrict__ W, double dt,
+                                                   double *__restrict__ acoef) {
+  constexpr int NS = op_ncoef(OP), DIAG = OP == OPK_VISC ? 3 : 9;
+  for (long long c = (long long)blockIdx.x * RB + threadIdx.x; c < d.N; c += (long long)gridDim.x * RB) {
+#pragma unroll
+    for (int s = 0; s < NS; s++)
+      acoef[s * d.N + c] = s == DIAG ? fma(dt, coef[s * d.N + c], W[c]) : dt * coef[s * d.N + c];
+  }
+}
+
+// y = A p with A from k_assemble_A ; alpha = r.z / p.y
+template <int OP>
+__global__ void __launch_bounds__(RB, 4) k_spmv_a(Dims d, const double *__restrict__ acoef,
+                                               const double *__restrict__ p, double *__restrict__ y,
+                                               double *partials, unsigned int *counter, PcgState *st) {
+  if (st->status != PCG_RUNNING) return;
+  double v[1] = {0.0};
+  for (long long c = (long long)blockIdx.x * RB + threadIdx.x; c < d.N; c += (long long)gridDim.x * RB) {
+    int i, j, k;
+    cell_coords(d, c, i, j, k);
+    Nbr n = neighbours(d, i, j, k);
+    const double yv = S_apply<OP, double>(d, acoef, p, c, n);
+    y[c] = yv;
+    v[0] = fma(p[c], yv, v[0]);
+  }
+  double tot[1];
+  if (grid_sum<1, RB>(v, partials, counter, tot) && threadIdx.x == 0) {
+    double pAp = tot[0];
+    st->pAp = pAp;
+    if (!(pAp > 0.0) || !isfinite(pAp)) st->status = PCG_BREAKDOWN;
+    else st->alpha = st->rr / pAp;
+  }
+}
+
 // FP32 y = A p for the symmetric 19-point conduction operator, marching along phi like
 // k_rkl2_stage_mix_march (rkl2.cu): a CTA owns a 32 x 8 (r, theta) tile and a chunk of
 // phi planes, one thread per cell of the tile and its halo stages p and the
@@ -764,6 +803,7 @@ template <typename T>
 struct PcgFields {
   T *x, *r, *p, *y, *z, *dinv;
   const T *coef, *W, *LU;
+  const double *acoef;  // A = W + dt S for the FP64 iteration (NULL: y = W p + dt S p)
 };
 
 static int state_upload(rkl_ctx *ctx, double rtol, int maxit) {
@@ -843,6 +883,9 @@ static int pcg_loop(rkl_ctx *ctx, const PcgFields<T> &f, double dt, int pc, int 
           k_spmv_march<<<mgrid, MTHREADS, 0, ctx->stream>>>(d, (const float *)f.coef, (const float *)f.W, (float)dt,
                                                            (const float *)f.p, (float *)f.y, ctx->partials,
                                                            ctx->counter, ctx->d_state, kchunk);
+        else if (f.acoef)
+          k_spmv_a<OP><<<g, RB, 0, ctx->stream>>>(d, f.acoef, (const double *)f.p, (double *)f.y, ctx->partials,
+                                                  ctx->counter, ctx->d_state);
         else
           k_spmv<OP, T><<<g, RB, 0, ctx->stream>>>(d, f.coef, f.W, tdt, f.p, f.y, ctx->partials, ctx->counter,
                                                    ctx->d_state);
@@ -887,7 +930,24 @@ static int pcg_run(rkl_ctx *ctx, double *x, const double *u, const double *x0, d
     return rc;
   if ((rc = state_upload(ctx, rtol, maxit))) return rc;
   const unsigned g = stride_grid(ctx);
-  PcgFields<double> f{x, ctx->r, ctx->p, ctx->y, ctx->zbuf, ctx->dinv, ctx->coef, ctx->W, ctx->LU};
+  if (op_ncoef(OP) > ctx->acoef_slots) {
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(ctx->acoef);
+    ctx->acoef = nullptr;
+    ctx->acoef_slots = 0;
+    if ((rc = cuda_check(ctx, cudaMalloc(&ctx->acoef, op_ncoef(OP) * N * sizeof(double)), "alloc A")))
+      return rc;
+    ctx->acoef_slots = op_ncoef(OP);
+  }
+  if (!ctx->acoef_valid || ctx->acoef_dt != dt) {
+    ProfScope prof(ctx, RKL_K_PCG_INIT);
+    k_assemble_A<OP><<<g, RB, 0, ctx->stream>>>(d, ctx->coef, ctx->W, dt, ctx->acoef);
+    ctx->launches += 1;
+    if ((rc = cuda_check(ctx, cudaGetLastError(), "A assembly launch"))) return rc;
+    ctx->acoef_valid = 1;
+    ctx->acoef_dt = dt;
+  }
+  PcgFields<double> f{x, ctx->r, ctx->p, ctx->y, ctx->zbuf, ctx->dinv, ctx->coef, ctx->W, ctx->LU, ctx->acoef};
   {
     ProfScope prof(ctx, RKL_K_PCG_INIT);
     k_r0<OP><<<g, RB, 0, ctx->stream>>>(d, ctx->coef, ctx->W, dt, u, x0 ? x0 : u, ctx->r,
@@ -929,7 +989,8 @@ static int pcg_run_mixed(rkl_ctx *ctx, double *x, const double *u, const double 
       (rc = ensure_fbuffer(ctx, &ctx->e32, N, "PCG e32")) || (rc = ensure_fbuffer(ctx, &ctx->dinv32, N, "PCG d32")))
     return rc;
   const unsigned g = stride_grid(ctx);
-  PcgFields<float> f{ctx->e32, ctx->r32, ctx->p32, ctx->y32, ctx->z32, ctx->dinv32, ctx->coef32, ctx->W32, ctx->LU32};
+  PcgFields<float> f{ctx->e32, ctx->r32, ctx->p32, ctx->y32, ctx->z32, ctx->dinv32, ctx->coef32, ctx->W32, ctx->LU32,
+                     nullptr};
   // x may share its buffer with u: keep u^n for the right-hand side W u^n of every
   // outer residual (the FP64 buffer p is not used by the mixed solve)
   double *un = ctx->p;
