@@ -485,13 +485,13 @@ def variants_report(wl, torch):
     return out
 
 
-def accuracy_report(wl, torch):
+def accuracy_report(wl, torch, ratios=RATIOS):
     """Relative L2 error of one large step of each method against the semi-discrete
     solution exp(dt M) T, approximated by 64 RKL2 sub-steps of dt/64 (FP64 GPU path)."""
     R = wl.R
     dte = wl.ctx_c.set_conduction(wl.T, wl.b, wl.n, beta_tcut=BETA_TCUT)
     out = {}
-    for ratio in RATIOS:
+    for ratio in ratios:
         ref = wl.T.clone()
         for _ in range(64):
             wl.ctx_c.rkl2_superstep(ref, ratio * dte / 64, dte)
@@ -504,6 +504,46 @@ def accuracy_report(wl, torch):
         e_be = torch.linalg.vector_norm(wl.u - ref).item() / torch.linalg.vector_norm(ref).item()
         out[str(int(ratio))] = {"rkl2_rel_l2": e_rkl, "be_rel_l2": e_be,
                                 "change_rel_l2": nref / torch.linalg.vector_norm(ref).item()}
+    return out
+
+
+def seeds_report(wl, torch, seeds=(2, 3)):
+    """The same conduction paths on the other seeded inputs (the headline uses seed 1):
+    stage counts, PCG iterations, ms per large step and accuracy at 1000 dt_exp."""
+    from paper_1610_01265_gb300 import synth
+
+    R = wl.R
+    nr, nth, nph = GRID
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {}
+    T0, b0, n0 = wl.T.clone(), wl.b.clone(), wl.n.clone()
+    try:
+        for seed in seeds:
+            c = synth.conduction_case(nr, nth, nph, seed)
+            wl.T.copy_(torch.from_numpy(c["T"].reshape(-1)))
+            wl.b.copy_(torch.from_numpy(c["bhat"].reshape(-1)))
+            wl.n.copy_(torch.from_numpy(np.array(c["n"]).reshape(-1)))
+            r = {"accuracy_1000": accuracy_report(wl, torch, ratios=(1000.0,))["1000"]}
+            dte = wl.ctx_c.set_conduction(wl.T, wl.b, wl.n, beta_tcut=BETA_TCUT)
+            wl.u.copy_(wl.T)
+            e0.record()
+            s = wl.ctx_c.rkl2_superstep(wl.u, 1000 * dte, dte)
+            e1.record()
+            torch.cuda.synchronize()
+            r["rkl2_1000"] = {"s": s, "ms": e0.elapsed_time(e1)}
+            for pc, name in ((R.RKL_PC_JACOBI, "jacobi"), (R.RKL_PC_BILU0, "bilu0")):
+                wl.u.copy_(wl.T)
+                e0.record()
+                code, its, rel = wl.ctx_c.be_pcg_solve(wl.u, 1000 * dte, pc=pc, block=BLOCK, rtol=RTOL, maxit=MAXIT)
+                e1.record()
+                torch.cuda.synchronize()
+                r[f"be_{name}_1000"] = {"iters": its[0], "ms": e0.elapsed_time(e1), "converged": code == R.RKL_OK}
+            out[str(seed)] = r
+    finally:
+        wl.T.copy_(T0)
+        wl.b.copy_(b0)
+        wl.n.copy_(n0)
+        wl.ctx_c.set_conduction(wl.T, wl.b, wl.n, beta_tcut=BETA_TCUT)
     return out
 
 
@@ -980,6 +1020,7 @@ def main():
             detail["mixed_precision"] = mixed_report(wl, R, torch)
             detail["sec6_variants"] = variants_report(wl, torch)
             detail["flux_form"] = flux_report(wl, torch)
+            detail["other_seeds"] = seeds_report(wl, torch)
 
     e2e = None
     if not args.no_e2e:

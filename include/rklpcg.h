@@ -63,7 +63,7 @@ enum { RKL_OP_CONDUCTION = 0, RKL_OP_VISCOSITY = 1 };
 enum { RKL_PC_JACOBI = 1, RKL_PC_BILU0 = 2 };
 enum { RKL_F64 = 0, RKL_F32MIX = 1 };
 
-#define RKL_BETA_TCUT 1 /* set_coeffs: evaluate kappa at max(T, 5e5 K) (Sec. 4.1 beta_Tcut) */
+#define RKL_BETA_TCUT 1 /* set_coeffs: kappa times (T / 5e5 K)^{5/2} below 5e5 K (Sec. 4.1 beta_Tcut) */
 #define RKL_FLUX_FORM 2 /* set_coeffs (conduction): non-symmetric flux form, see set_coeffs */
 #define RKL_FORCE_ODD 1 /* rkl2_superstep: round s up to an odd number (Sec. 3) */
 

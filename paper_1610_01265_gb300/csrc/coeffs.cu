@@ -50,8 +50,12 @@ __global__ void k_cell_cond(Dims d, Geo g, const double *__restrict__ T,
     t = 1.0;
     nn = 1.0;
   }
-  double te = ((flags & RKL_BETA_TCUT) && t < RKL_TCUT) ? RKL_TCUT : t;
-  kappa[c] = kappa0 * te * te * sqrt(te);
+  double kap = kappa0 * t * t * sqrt(t);
+  if ((flags & RKL_BETA_TCUT) && t < RKL_TCUT) {  // beta_Tcut = (T / T_cut)^{5/2} (Sec. 4.1)
+    const double q = t / RKL_TCUT;
+    kap *= q * q * sqrt(q);
+  }
+  kappa[c] = kap;
   double V = g.v3[i] * g.dcos[j] * g.dph;
   double w = 3.0 * RKL_KBOLTZ * nn * V;
   W[c] = w;

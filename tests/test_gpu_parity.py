@@ -277,3 +277,24 @@ def test_error_paths(R, torch_cuda):
     assert e.value.code == R.RKL_EINVAL
     assert R.rkl2_stage_count(100.0) == 20 and R.rkl2_stage_count(100.0, R.RKL_FORCE_ODD) == 21
     ctx.close()
+
+
+def test_beta_tcut_operator(oracle_mod, R, torch_cuda):
+    """RKL_BETA_TCUT: kappa0 T^{5/2} (T / 5e5 K)^{5/2} below 5e5 K (Sec. 4.1); the seeded
+    case dips below 5e5 K near r = 1, so the factor is exercised."""
+    O = oracle_mod
+    dims = (64, 16, 32)
+    c = synth.conduction_case(*dims, seed=3)
+    assert (c["T"] < 5e5).sum() > 50
+    g = O.Grid(c["rf"], dims[1], dims[2])
+    S, W = O.assemble_conduction(g, c["T"], c["bhat"], c["n"], beta_tcut=True)
+    ctx = R.Context(c["rf"], dims[1], dims[2])
+    dev = lambda a: torch_cuda.from_numpy(np.array(a, dtype=np.float64)).cuda().view(-1)  # noqa: E731
+    dte = ctx.set_conduction(dev(c["T"]), dev(c["bhat"]), dev(c["n"]), beta_tcut=True)
+    assert dte == pytest.approx(O.gershgorin_dt(g, S, W)[0], rel=1e-13)
+    u = synth.random_field(g.shape, 9)
+    Fu = dev(np.zeros(g.N))
+    ctx.apply_F(dev(u), Fu)
+    F_o = O.apply_F(g, S, W, u)
+    assert np.linalg.norm(Fu.cpu().numpy() - F_o.ravel()) <= 1e-12 * np.linalg.norm(F_o)
+    ctx.close()
