@@ -235,6 +235,8 @@ int rkl_create(rkl_ctx **out, const rkl_grid *g, int prec, void *stream) {
 int rkl_destroy(rkl_ctx *ctx) {
   if (!ctx) return RKL_OK;
   cudaStreamSynchronize(ctx->stream);
+  if (ctx->sts_exec) cudaGraphExecDestroy(ctx->sts_exec);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   prof_release(ctx);
   double *bufs[] = {ctx->geo_buf, ctx->coef, ctx->W, ctx->invW, ctx->scratch, ctx->M0, ctx->Ya, ctx->Yb,
                     ctx->r, ctx->p, ctx->y, ctx->zbuf, ctx->dinv, ctx->partials, ctx->LU, ctx->stage, ctx->stage2,
@@ -277,6 +279,7 @@ int set_coeffs(rkl_ctx *ctx, int op, const double *a, const double *b, const dou
   ctx->op = -1;
   ctx->lu_valid = 0;
   ctx->acoef_valid = 0;
+  ctx->epoch += 1;
   int rc = ensure_buffer(ctx, &ctx->scratch, 10 * N, "alloc set_coeffs scratch");
   if (rc) return rc;
   if (op_ncoef(kind) > ctx->coef_slots) {  // full rows need 19 slots
@@ -365,6 +368,114 @@ int apply_F(rkl_ctx *ctx, const double *u, double *Fu, int ncomp) {
   return RKL_OK;
 }
 
+namespace {
+
+// the stage launches of one super-step (Fig. 2) for ncomp components at du
+int rkl2_stages(rkl_ctx *ctx, double *du, int ncomp, int s, double dt, double w1) {
+  const size_t N = (size_t)ctx->d.N;
+  int rc;
+  if (ctx->prec == RKL_F32MIX) {
+    for (int q = 0; q < ncomp; q++) {
+      double *Y0 = du + q * N;
+      if ((rc = launch_rkl2_first_mix(ctx, Y0, ctx->M0f, ctx->da32, w1 / 3.0 * dt))) return rc;
+      float *dm1 = ctx->da32, *dm2 = nullptr;
+      for (int j = 2; j <= s; j++) {
+        double mu = (2.0 * j - 1.0) / j * rkl_b(j) / rkl_b(j - 1);
+        double nu = -(j - 1.0) / j * rkl_b(j) / rkl_b(j - 2);
+        double mut = w1 * mu;
+        double gt = -(1.0 - rkl_b(j - 1)) * mut;
+        const bool last = j == s;
+        float *out = last ? nullptr : (j == 2 ? ctx->db32 : dm2);
+        if ((rc = launch_rkl2_stage_mix(ctx, dm1, dm2, ctx->M0f, out, last ? Y0 : nullptr, mu, nu, mut * dt,
+                                        (mut + gt) * dt)))
+          return rc;
+        dm2 = dm1;
+        dm1 = out;
+      }
+    }
+    return RKL_OK;
+  }
+  for (int q = 0; q < ncomp; q++) {
+    double *Y0 = du + q * N;
+    if ((rc = launch_rkl2_stage1(ctx, Y0, ctx->M0, ctx->Ya, w1 / 3.0 * dt))) return rc;
+    double *ym1 = ctx->Ya, *ym2 = Y0;
+    for (int j = 2; j <= s; j++) {
+      double mu = (2.0 * j - 1.0) / j * rkl_b(j) / rkl_b(j - 1);
+      double nu = -(j - 1.0) / j * rkl_b(j) / rkl_b(j - 2);
+      double mut = w1 * mu;
+      double gt = -(1.0 - rkl_b(j - 1)) * mut;
+      double *out = (j == s) ? Y0 : (j == 2 ? ctx->Yb : ym2);
+      if ((rc = launch_rkl2_stage(ctx, ym1, ym2, Y0, ctx->M0, out, mu, nu, mut * dt, gt * dt))) return rc;
+      ym2 = ym1;
+      ym1 = out;
+    }
+  }
+  return RKL_OK;
+}
+
+// The same launches through a CUDA graph: a call that repeats the last one (same stage
+// count, components, field, precision, operator, dt and frozen coefficients) replays the
+// instantiated graph; otherwise the launches are captured again and the executable graph
+// is updated in place (or re-instantiated when its shape changed).
+int rkl2_stages_graph(rkl_ctx *ctx, double *du, int ncomp, int s, double dt, double w1) {
+  const bool same_shape = ctx->sts_exec && ctx->sts_s == s && ctx->sts_ncomp == ncomp && ctx->sts_u == du &&
+                          ctx->sts_prec == ctx->prec && ctx->sts_op == ctx->op;
+  if (same_shape && ctx->sts_dt == dt && ctx->sts_epoch == ctx->epoch) {
+    ctx->launches += ctx->sts_nkern;
+    return cuda_check(ctx, cudaGraphLaunch(ctx->sts_exec, ctx->stream), "super-step graph launch");
+  }
+  // capture on a private stream (the caller's may be the legacy default stream, which
+  // cannot be captured); the graph is then launched on the caller's stream
+  int rc = RKL_OK;
+  if (!ctx->cap_stream &&
+      (rc = cuda_check(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking), "capture stream")))
+    return rc;
+  const long long l0 = ctx->launches;
+  cudaStream_t user = ctx->stream;
+  ctx->stream = ctx->cap_stream;
+  rc = cuda_check(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal), "super-step capture");
+  if (rc) {
+    ctx->stream = user;
+    return rc;
+  }
+  const int rc_launch = rkl2_stages(ctx, du, ncomp, s, dt, w1);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
+  ctx->stream = user;
+  if (rc_launch || e != cudaSuccess || !graph) {
+    if (graph) cudaGraphDestroy(graph);
+    ctx->launches = l0;
+    return rc_launch ? rc_launch : cuda_check(ctx, e, "super-step capture");
+  }
+  bool updated = false;
+  if (same_shape) {
+    cudaGraphExecUpdateResultInfo info;
+    updated = cudaGraphExecUpdate(ctx->sts_exec, graph, &info) == cudaSuccess;
+    if (!updated) cudaGetLastError();
+  }
+  if (!updated) {
+    if (ctx->sts_exec) cudaGraphExecDestroy(ctx->sts_exec);
+    ctx->sts_exec = nullptr;
+    rc = cuda_check(ctx, cudaGraphInstantiate(&ctx->sts_exec, graph, 0), "super-step graph instantiate");
+  }
+  cudaGraphDestroy(graph);
+  if (rc) {
+    ctx->sts_exec = nullptr;
+    return rc;
+  }
+  ctx->sts_s = s;
+  ctx->sts_ncomp = ncomp;
+  ctx->sts_u = du;
+  ctx->sts_prec = ctx->prec;
+  ctx->sts_op = ctx->op;
+  ctx->sts_dt = dt;
+  ctx->sts_epoch = ctx->epoch;
+  ctx->sts_nkern = ctx->launches - l0;
+  return cuda_check(ctx, cudaGraphLaunch(ctx->sts_exec, ctx->stream), "super-step graph launch");
+}
+
+}  // namespace
+
 int rkl2_superstep(rkl_ctx *ctx, double *u, int ncomp, double dt, double dt_exp, int s, int flags,
                    int *s_used) {
   if (!ctx) return RKL_EINVAL;
@@ -385,51 +496,18 @@ int rkl2_superstep(rkl_ctx *ctx, double *u, int ncomp, double dt, double dt_exp,
   bool su;
   if (!is_device_ptr(u) && (rc = ensure_stage(ctx, tot))) return rc;
   if ((rc = to_device(ctx, u, tot, 0, true, &du, &su))) return rc;
+  if (ctx->prec == RKL_F32MIX &&
+      ((rc = ensure_fbuffer(ctx, &ctx->M0f, N, "alloc M0 (FP32)")) ||
+       (rc = ensure_fbuffer(ctx, &ctx->da32, N, "alloc increments")) ||
+       (rc = ensure_fbuffer(ctx, &ctx->db32, N, "alloc increments"))))
+    return rc;
   const double w1 = 4.0 / ((double)s * s + s - 2.0);
-  if (ctx->prec == RKL_F32MIX) {
-    if ((rc = ensure_fbuffer(ctx, &ctx->M0f, N, "alloc M0 (FP32)")) ||
-        (rc = ensure_fbuffer(ctx, &ctx->da32, N, "alloc increments")) ||
-        (rc = ensure_fbuffer(ctx, &ctx->db32, N, "alloc increments")))
-      return rc;
-    for (int q = 0; q < ncomp; q++) {
-      double *Y0 = du + q * N;
-      if ((rc = launch_rkl2_first_mix(ctx, Y0, ctx->M0f, ctx->da32, w1 / 3.0 * dt))) return rc;
-      float *dm1 = ctx->da32, *dm2 = nullptr;
-      for (int j = 2; j <= s; j++) {
-        double mu = (2.0 * j - 1.0) / j * rkl_b(j) / rkl_b(j - 1);
-        double nu = -(j - 1.0) / j * rkl_b(j) / rkl_b(j - 2);
-        double mut = w1 * mu;
-        double gt = -(1.0 - rkl_b(j - 1)) * mut;
-        const bool last = j == s;
-        float *out = last ? nullptr : (j == 2 ? ctx->db32 : dm2);
-        if ((rc = launch_rkl2_stage_mix(ctx, dm1, dm2, ctx->M0f, out, last ? Y0 : nullptr, mu, nu, mut * dt,
-                                        (mut + gt) * dt)))
-          return rc;
-        dm2 = dm1;
-        dm1 = out;
-      }
-    }
-    if (s_used) *s_used = s;
-    if (su) {
-      if ((rc = from_device(ctx, u, du, tot))) return rc;
-      return sync(ctx, "rkl2_superstep");
-    }
-    return RKL_OK;
-  }
-  for (int q = 0; q < ncomp; q++) {
-    double *Y0 = du + q * N;
-    if ((rc = launch_rkl2_stage1(ctx, Y0, ctx->M0, ctx->Ya, w1 / 3.0 * dt))) return rc;
-    double *ym1 = ctx->Ya, *ym2 = Y0;
-    for (int j = 2; j <= s; j++) {
-      double mu = (2.0 * j - 1.0) / j * rkl_b(j) / rkl_b(j - 1);
-      double nu = -(j - 1.0) / j * rkl_b(j) / rkl_b(j - 2);
-      double mut = w1 * mu;
-      double gt = -(1.0 - rkl_b(j - 1)) * mut;
-      double *out = (j == s) ? Y0 : (j == 2 ? ctx->Yb : ym2);
-      if ((rc = launch_rkl2_stage(ctx, ym1, ym2, Y0, ctx->M0, out, mu, nu, mut * dt, gt * dt))) return rc;
-      ym2 = ym1;
-      ym1 = out;
-    }
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if ((rc = cuda_check(ctx, cudaStreamIsCapturing(ctx->stream, &cap), "stream capture query"))) return rc;
+  if (ctx->prof_on || cap != cudaStreamCaptureStatusNone || s < 4) {
+    if ((rc = rkl2_stages(ctx, du, ncomp, s, dt, w1))) return rc;
+  } else if ((rc = rkl2_stages_graph(ctx, du, ncomp, s, dt, w1))) {
+    return rc;
   }
   if (s_used) *s_used = s;
   if (su) {

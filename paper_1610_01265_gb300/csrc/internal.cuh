@@ -181,6 +181,15 @@ struct rkl_ctx {
   double prof_ms[RKL_K_COUNT] = {};
   long long prof_n[RKL_K_COUNT] = {};
 
+  // CUDA graph of the last super-step's stage launches (rkl2_superstep), replayed when the
+  // same call repeats; epoch counts set_coeffs calls (a new operator forces a re-capture)
+  cudaGraphExec_t sts_exec = nullptr;
+  cudaStream_t cap_stream = nullptr;  // private stream the launches are captured on
+  int sts_s = 0, sts_ncomp = 0, sts_prec = -1, sts_op = -1;
+  const double *sts_u = nullptr;
+  double sts_dt = 0.0;
+  long long sts_epoch = -1, sts_nkern = 0, epoch = 0;
+
   // host-pointer staging
   double *stage = nullptr;
   size_t stage_cap = 0;  // doubles

@@ -298,3 +298,32 @@ def test_beta_tcut_operator(oracle_mod, R, torch_cuda):
     F_o = O.apply_F(g, S, W, u)
     assert np.linalg.norm(Fu.cpu().numpy() - F_o.ravel()) <= 1e-12 * np.linalg.norm(F_o)
     ctx.close()
+
+
+def test_superstep_graph_replay_and_invalidation(oracle_mod, R, torch_cuda):
+    """Repeated super-steps replay a captured CUDA graph; a new dt, new coefficients, another
+    field or a switch of operator form must not reuse stale launches."""
+    O = oracle_mod
+    dims = (16, 12, 24)
+    c = synth.conduction_case(*dims, seed=5)
+    g = O.Grid(c["rf"], dims[1], dims[2])
+    dev = lambda a: torch_cuda.from_numpy(np.array(a, dtype=np.float64)).cuda().view(-1)  # noqa: E731
+    ctx = R.Context(c["rf"], dims[1], dims[2])
+    T2 = c["T"] * (1.0 + 0.1 * synth.random_field(g.shape, 3, 0.0, 1.0))
+    cases = [(c["T"], 100.0, False), (c["T"], 100.0, False), (c["T"], 300.0, False), (c["T"], 100.0, False),
+             (T2, 100.0, False), (T2, 100.0, True), (c["T"], 100.0, False)]
+    u = dev(c["T"])
+    other = dev(c["T"])
+    for q, (Tc, ratio, flux) in enumerate(cases):
+        S, W = O.assemble_conduction(g, Tc, c["bhat"], c["n"], flux_form=flux)
+        dte = ctx.set_conduction(dev(Tc), dev(c["bhat"]), dev(c["n"]), flux_form=flux)
+        target = other if q == 3 else u  # q == 3: same call on another field
+        target.copy_(dev(c["T"]))
+        s = ctx.rkl2_superstep(target, ratio * dte, dte)
+        ref = O.rkl2_superstep(g, S, W, c["T"], ratio * dte, s)
+        assert np.linalg.norm(target.cpu().numpy() - ref.ravel()) <= 1e-12 * np.linalg.norm(ref), q
+    n0 = ctx.kernel_launches
+    u.copy_(dev(c["T"]))
+    s = ctx.rkl2_superstep(u, 100.0 * dte, dte)
+    assert ctx.kernel_launches - n0 == s  # first stage + s - 1 stages, counted on replay too
+    ctx.close()
