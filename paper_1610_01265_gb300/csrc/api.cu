@@ -236,6 +236,7 @@ int rkl_destroy(rkl_ctx *ctx) {
   if (!ctx) return RKL_OK;
   cudaStreamSynchronize(ctx->stream);
   if (ctx->sts_exec) cudaGraphExecDestroy(ctx->sts_exec);
+  if (ctx->pcg_exec) cudaGraphExecDestroy(ctx->pcg_exec);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   prof_release(ctx);
   double *bufs[] = {ctx->geo_buf, ctx->coef, ctx->W, ctx->invW, ctx->scratch, ctx->M0, ctx->Ya, ctx->Yb,
@@ -455,6 +456,7 @@ int rkl2_stages_graph(rkl_ctx *ctx, double *du, int ncomp, int s, double dt, dou
   }
   if (!updated) {
     if (ctx->sts_exec) cudaGraphExecDestroy(ctx->sts_exec);
+  if (ctx->pcg_exec) cudaGraphExecDestroy(ctx->pcg_exec);
     ctx->sts_exec = nullptr;
     rc = cuda_check(ctx, cudaGraphInstantiate(&ctx->sts_exec, graph, 0), "super-step graph instantiate");
   }

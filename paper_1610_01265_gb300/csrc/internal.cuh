@@ -86,7 +86,7 @@ struct PcgState {
   int iters;
   int maxit;
   int status;      // 0 running, 1 converged, 2 breakdown, 3 maxit reached
-  int pad;
+  int loops;       // chunks run by the graph-driven loop (device-side bound)
 };
 
 enum { PCG_RUNNING = 0, PCG_CONVERGED = 1, PCG_BREAKDOWN = 2, PCG_MAXIT = 3 };
@@ -189,6 +189,12 @@ struct rkl_ctx {
   const double *sts_u = nullptr;
   double sts_dt = 0.0;
   long long sts_epoch = -1, sts_nkern = 0, epoch = 0;
+
+  // CUDA graph of the PCG loop (a WHILE node over chunks of iterations), kept for the
+  // last solve's kernels, fields, dt, preconditioner and operator
+  cudaGraphExec_t pcg_exec = nullptr;
+  unsigned long long pcg_key = 0;
+  int pcg_kpc = 0;  // kernels per chunk of the cached graph (including the condition kernel)
 
   // host-pointer staging
   double *stage = nullptr;

@@ -845,74 +845,188 @@ static void pcg_first(rkl_ctx *ctx, const PcgFields<T> &f, int pc) {
   }
 }
 
-// Fig. 1's loop, queued in chunks of 8 iterations, until the device status leaves
-// "running" (converged, breakdown, maxit)
+// Launch configuration of the iteration kernels of one solve.
+struct LoopCfg {
+  unsigned g, nblk;
+  size_t smem;
+  bool march;
+  dim3 mgrid;
+  int kchunk;
+};
+
 template <int OP, typename T>
-static int pcg_loop(rkl_ctx *ctx, const PcgFields<T> &f, double dt, int pc, int maxit) {
+static LoopCfg loop_cfg(const rkl_ctx *ctx, int pc) {
   const Dims &d = ctx->d;
-  const long long N = d.N;
-  const unsigned g = stride_grid(ctx);
-  const unsigned nblk = (unsigned)ctx->plan.ngroups;
-  const size_t smem = pc == RKL_PC_BILU0 ? ilu_smem(ctx, sizeof(T)) : 0;
-  const T tdt = (T)dt;
-  const int chunk = 8;
-  int it_prev = 0, rc;
+  LoopCfg L;
+  L.g = stride_grid(ctx);
+  L.nblk = (unsigned)ctx->plan.ngroups;
+  L.smem = pc == RKL_PC_BILU0 ? ilu_smem(ctx, sizeof(T)) : 0;
   // FP32 symmetric conduction: the phi-marching y = A p when its CTAs fit the partials
   const int nbx = (d.nr + MR - 1) / MR, nby = (d.nth + MT - 1) / MT;
   const int nz = std::max(1, std::min(d.nph, (8 * ctx->nsm + nbx * nby - 1) / (nbx * nby)));
-  const int kchunk = (d.nph + nz - 1) / nz;
-  const dim3 mgrid(nbx, nby, (d.nph + kchunk - 1) / kchunk);
-  const bool march = std::is_same<T, float>::value && OP == OPK_COND &&
-                     (long long)mgrid.x * mgrid.y * mgrid.z <= (long long)ctx->npart;
+  L.kchunk = (d.nph + nz - 1) / nz;
+  L.mgrid = dim3(nbx, nby, (d.nph + L.kchunk - 1) / L.kchunk);
+  L.march = std::is_same<T, float>::value && OP == OPK_COND &&
+            (long long)L.mgrid.x * L.mgrid.y * L.mgrid.z <= (long long)ctx->npart;
+  return L;
+}
+
+// `chunk` iterations of Fig. 1 on ctx->stream; every kernel returns at once when the
+// device status has left "running"
+template <int OP, typename T>
+static void queue_chunk(rkl_ctx *ctx, const PcgFields<T> &f, double dt, int pc, const LoopCfg &L, int chunk) {
+  const Dims &d = ctx->d;
+  const long long N = d.N;
+  const T tdt = (T)dt;
+  for (int q = 0; q < chunk; q++) {
+    {
+      ProfScope prof(ctx, RKL_K_SPMV, q);
+      if (L.march)
+        k_spmv_march<<<L.mgrid, MTHREADS, 0, ctx->stream>>>(d, (const float *)f.coef, (const float *)f.W, (float)dt,
+                                                             (const float *)f.p, (float *)f.y, ctx->partials,
+                                                             ctx->counter, ctx->d_state, L.kchunk);
+      else if (f.acoef)
+        k_spmv_a<OP><<<L.g, RB, 0, ctx->stream>>>(d, f.acoef, (const double *)f.p, (double *)f.y, ctx->partials,
+                                                  ctx->counter, ctx->d_state);
+      else
+        k_spmv<OP, T><<<L.g, RB, 0, ctx->stream>>>(d, f.coef, f.W, tdt, f.p, f.y, ctx->partials, ctx->counter,
+                                                   ctx->d_state);
+    }
+    if (pc == RKL_PC_JACOBI) {
+      {
+        ProfScope prof(ctx, RKL_K_PCG_UPDATE, q);
+        k_update_jacobi<T><<<L.g, RB, 0, ctx->stream>>>(N, f.x, f.p, f.r, f.y, f.dinv, ctx->partials,
+                                                        ctx->counter, ctx->d_state);
+      }
+      ProfScope prof(ctx, RKL_K_PCG_PUPDATE, q);
+      k_pupdate_jacobi<T><<<L.g, RB, 0, ctx->stream>>>(N, f.r, f.dinv, f.p, ctx->d_state);
+    } else {
+      {
+        ProfScope prof(ctx, RKL_K_PCG_UPDATE, q);
+        k_xr_update<T><<<L.g, RB, 0, ctx->stream>>>(N, f.x, f.p, f.r, f.y, ctx->d_state);
+      }
+      {
+        ProfScope prof(ctx, RKL_K_BILU_APPLY, q);
+        k_bilu_apply<ilu_op(OP), T><<<L.nblk, AB, L.smem, ctx->stream>>>(d, ctx->plan, f.LU, f.r, f.z,
+                                                                         ctx->partials, ctx->counter,
+                                                                         ctx->d_state, 0);
+      }
+      ProfScope prof(ctx, RKL_K_PCG_PUPDATE, q);
+      k_pupdate_z<T><<<L.g, RB, 0, ctx->stream>>>(N, f.z, f.p, ctx->d_state, 0);
+    }
+  }
+}
+
+// Condition of the graph-driven loop: run another chunk while the solve is running and
+// below maxit, and never more than maxit / chunk + 2 chunks (a bound that does not rely
+// on the iteration state)
+__global__ void k_pcg_continue(PcgState *st, int chunk, cudaGraphConditionalHandle h) {
+  if (threadIdx.x != 0) return;
+  const int l = ++st->loops;
+  const bool go = st->status == PCG_RUNNING && st->iters < st->maxit && l <= st->maxit / chunk + 2;
+  cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+constexpr int PCG_CHUNK = 8;
+
+// Fig. 1's loop as one CUDA graph: a WHILE node whose body is a chunk of iterations
+// followed by k_pcg_continue; launched once, so the host waits once per solve.  The
+// executable graph is kept for the next solve with the same kernels and arguments.
+template <int OP, typename T>
+static int pcg_loop_graph(rkl_ctx *ctx, const PcgFields<T> &f, double dt, int pc, const LoopCfg &L) {
+  unsigned long long key = 1469598103934665603ULL;  // FNV-1a over the arguments
+  auto mix = [&](const void *p, size_t n) {
+    const unsigned char *b = (const unsigned char *)p;
+    for (size_t q = 0; q < n; q++) key = (key ^ b[q]) * 1099511628211ULL;
+  };
+  const int op = OP, tsize = (int)sizeof(T);
+  const void *ptrs[] = {f.x, f.r, f.p, f.y, f.z, f.dinv, f.coef, f.W, f.LU, f.acoef, ctx->partials, ctx->counter,
+                        ctx->d_state, ctx->plan_buf};
+  mix(&op, sizeof op);
+  mix(&tsize, sizeof tsize);
+  mix(&pc, sizeof pc);
+  mix(&dt, sizeof dt);
+  mix(ptrs, sizeof ptrs);
+  mix(&L.g, sizeof L.g);
+  mix(&L.nblk, sizeof L.nblk);
+  mix(&L.smem, sizeof L.smem);
+  mix(&L.march, sizeof L.march);
+  mix(&L.kchunk, sizeof L.kchunk);
+  int rc = RKL_OK;
+  if (!ctx->pcg_exec || ctx->pcg_key != key) {
+    if (ctx->pcg_exec) cudaGraphExecDestroy(ctx->pcg_exec);
+    ctx->pcg_exec = nullptr;
+    if (!ctx->cap_stream &&
+        (rc = cuda_check(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking), "capture stream")))
+      return rc;
+    cudaGraph_t graph = nullptr;
+    if ((rc = cuda_check(ctx, cudaGraphCreate(&graph, 0), "PCG graph"))) return rc;
+    cudaGraphConditionalHandle h;
+    cudaGraphNodeParams np = {};
+    cudaGraphNode_t node;
+    rc = cuda_check(ctx, cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault), "PCG graph");
+    if (!rc) {
+      np.type = cudaGraphNodeTypeConditional;
+      np.conditional.handle = h;
+      np.conditional.type = cudaGraphCondTypeWhile;
+      np.conditional.size = 1;
+      rc = cuda_check(ctx, cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np), "PCG graph");
+    }
+    if (!rc) {
+      cudaGraph_t body = np.conditional.phGraph_out[0];
+      cudaStream_t user = ctx->stream;
+      ctx->stream = ctx->cap_stream;
+      rc = cuda_check(ctx, cudaStreamBeginCaptureToGraph(ctx->stream, body, nullptr, nullptr, 0,
+                                                         cudaStreamCaptureModeThreadLocal), "PCG graph capture");
+      if (!rc) {
+        queue_chunk<OP, T>(ctx, f, dt, pc, L, PCG_CHUNK);
+        k_pcg_continue<<<1, 32, 0, ctx->stream>>>(ctx->d_state, PCG_CHUNK, h);
+        cudaGraph_t captured = nullptr;
+        rc = cuda_check(ctx, cudaStreamEndCapture(ctx->stream, &captured), "PCG graph capture");
+      }
+      ctx->stream = user;
+    }
+    if (!rc) rc = cuda_check(ctx, cudaGraphInstantiate(&ctx->pcg_exec, graph, 0), "PCG graph instantiate");
+    cudaGraphDestroy(graph);
+    if (rc) {
+      ctx->pcg_exec = nullptr;
+      return rc;
+    }
+    ctx->pcg_key = key;
+    ctx->pcg_kpc = PCG_CHUNK * (pc == RKL_PC_JACOBI ? 3 : 4) + 1;
+  }
+  if ((rc = cuda_check(ctx, cudaGraphLaunch(ctx->pcg_exec, ctx->stream), "PCG graph launch"))) return rc;
+  if ((rc = state_read(ctx))) return rc;
+  ctx->launches += (long long)ctx->h_state->loops * ctx->pcg_kpc;
+  return RKL_OK;
+}
+
+// Fig. 1's loop until the device status leaves "running" (converged, breakdown, maxit):
+// through the graph above, or -- while the per-kernel profiler is on or the caller's stream
+// is being captured -- queued by the host in chunks with a status read after each chunk
+template <int OP, typename T>
+static int pcg_loop(rkl_ctx *ctx, const PcgFields<T> &f, double dt, int pc, int maxit) {
+  const LoopCfg L = loop_cfg<OP, T>(ctx, pc);
+  int it_prev = 0, rc;
+  if ((rc = state_read(ctx))) return rc;
+  if (ctx->h_state->status != PCG_RUNNING || ctx->h_state->iters >= maxit) return RKL_OK;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if ((rc = cuda_check(ctx, cudaStreamIsCapturing(ctx->stream, &cap), "stream capture query"))) return rc;
+  if (!ctx->prof_on && cap == cudaStreamCaptureStatusNone) return pcg_loop_graph<OP, T>(ctx, f, dt, pc, L);
   // host-side bound: the device counts iterations and stops at maxit; should its status
   // ever stop advancing, the host stops queueing after maxit + 2 chunks
   long long queued = 0;
-  for (;;) {
-    if ((rc = state_read(ctx))) return rc;
+  for (bool first = true;; first = false) {
+    if (!first && (rc = state_read(ctx))) return rc;
     const PcgState &h = *ctx->h_state;
     if (ctx->prof_on) prof_settle(ctx, h.iters - it_prev, h.status == PCG_RUNNING, true);
     it_prev = h.iters;
     if (h.status != PCG_RUNNING || h.iters >= maxit) break;
-    if (queued > (long long)maxit + 2 * chunk)
+    if (queued > (long long)maxit + 2 * PCG_CHUNK)
       return set_error(ctx, RKL_ECUDA, "PCG: device iteration count is not advancing");
-    queued += chunk;
-    for (int q = 0; q < chunk; q++) {
-      {
-        ProfScope prof(ctx, RKL_K_SPMV, q);
-        if (march)
-          k_spmv_march<<<mgrid, MTHREADS, 0, ctx->stream>>>(d, (const float *)f.coef, (const float *)f.W, (float)dt,
-                                                           (const float *)f.p, (float *)f.y, ctx->partials,
-                                                           ctx->counter, ctx->d_state, kchunk);
-        else if (f.acoef)
-          k_spmv_a<OP><<<g, RB, 0, ctx->stream>>>(d, f.acoef, (const double *)f.p, (double *)f.y, ctx->partials,
-                                                  ctx->counter, ctx->d_state);
-        else
-          k_spmv<OP, T><<<g, RB, 0, ctx->stream>>>(d, f.coef, f.W, tdt, f.p, f.y, ctx->partials, ctx->counter,
-                                                   ctx->d_state);
-      }
-      if (pc == RKL_PC_JACOBI) {
-        {
-          ProfScope prof(ctx, RKL_K_PCG_UPDATE, q);
-          k_update_jacobi<T><<<g, RB, 0, ctx->stream>>>(N, f.x, f.p, f.r, f.y, f.dinv, ctx->partials,
-                                                        ctx->counter, ctx->d_state);
-        }
-        ProfScope prof(ctx, RKL_K_PCG_PUPDATE, q);
-        k_pupdate_jacobi<T><<<g, RB, 0, ctx->stream>>>(N, f.r, f.dinv, f.p, ctx->d_state);
-      } else {
-        {
-          ProfScope prof(ctx, RKL_K_PCG_UPDATE, q);
-          k_xr_update<T><<<g, RB, 0, ctx->stream>>>(N, f.x, f.p, f.r, f.y, ctx->d_state);
-        }
-        {
-          ProfScope prof(ctx, RKL_K_BILU_APPLY, q);
-          k_bilu_apply<ilu_op(OP), T><<<nblk, AB, smem, ctx->stream>>>(d, ctx->plan, f.LU, f.r, f.z, ctx->partials,
-                                                               ctx->counter, ctx->d_state, 0);
-        }
-        ProfScope prof(ctx, RKL_K_PCG_PUPDATE, q);
-        k_pupdate_z<T><<<g, RB, 0, ctx->stream>>>(N, f.z, f.p, ctx->d_state, 0);
-      }
-    }
-    ctx->launches += (long long)chunk * (pc == RKL_PC_JACOBI ? 3 : 4);
+    queued += PCG_CHUNK;
+    queue_chunk<OP, T>(ctx, f, dt, pc, L, PCG_CHUNK);
+    ctx->launches += (long long)PCG_CHUNK * (pc == RKL_PC_JACOBI ? 3 : 4);
     if ((rc = cuda_check(ctx, cudaGetLastError(), "PCG iteration launch"))) return rc;
   }
   return RKL_OK;
