@@ -237,7 +237,9 @@ int rkl_destroy(rkl_ctx *ctx) {
   cudaStreamSynchronize(ctx->stream);
   if (ctx->sts_exec) cudaGraphExecDestroy(ctx->sts_exec);
   if (ctx->pcg_exec) cudaGraphExecDestroy(ctx->pcg_exec);
+  if (ctx->pcg_graph) cudaGraphDestroy(ctx->pcg_graph);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  if (ctx->pcg_stream) cudaStreamDestroy(ctx->pcg_stream);
   prof_release(ctx);
   double *bufs[] = {ctx->geo_buf, ctx->coef, ctx->W, ctx->invW, ctx->scratch, ctx->M0, ctx->Ya, ctx->Yb,
                     ctx->r, ctx->p, ctx->y, ctx->zbuf, ctx->dinv, ctx->partials, ctx->LU, ctx->stage, ctx->stage2,
@@ -253,6 +255,7 @@ int rkl_destroy(rkl_ctx *ctx) {
                     ctx->y32, ctx->z32, ctx->e32, ctx->dinv32, ctx->LU32};
   for (float *b : fbufs)
     if (b) cudaFree(b);
+  cudaGetLastError();  // a failed teardown call must not surface in another context's checks
   delete ctx;
   return RKL_OK;
 }
@@ -456,7 +459,7 @@ int rkl2_stages_graph(rkl_ctx *ctx, double *du, int ncomp, int s, double dt, dou
   }
   if (!updated) {
     if (ctx->sts_exec) cudaGraphExecDestroy(ctx->sts_exec);
-  if (ctx->pcg_exec) cudaGraphExecDestroy(ctx->pcg_exec);
+    cudaGetLastError();  // teardown of the previous graph is not an error of this call
     ctx->sts_exec = nullptr;
     rc = cuda_check(ctx, cudaGraphInstantiate(&ctx->sts_exec, graph, 0), "super-step graph instantiate");
   }
@@ -506,8 +509,11 @@ int rkl2_superstep(rkl_ctx *ctx, double *u, int ncomp, double dt, double dt_exp,
   const double w1 = 4.0 / ((double)s * s + s - 2.0);
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   if ((rc = cuda_check(ctx, cudaStreamIsCapturing(ctx->stream, &cap), "stream capture query"))) return rc;
-  if (ctx->prof_on || cap != cudaStreamCaptureStatusNone || s < 4) {
+  // kernels are loaded on their first launch (lazy module loading), which a stream capture
+  // does not allow: a context's first super-step runs without a graph
+  if (ctx->prof_on || cap != cudaStreamCaptureStatusNone || s < 4 || !ctx->sts_direct_done) {
     if ((rc = rkl2_stages(ctx, du, ncomp, s, dt, w1))) return rc;
+    ctx->sts_direct_done = 1;
   } else if ((rc = rkl2_stages_graph(ctx, du, ncomp, s, dt, w1))) {
     return rc;
   }

@@ -189,10 +189,13 @@ struct rkl_ctx {
   const double *sts_u = nullptr;
   double sts_dt = 0.0;
   long long sts_epoch = -1, sts_nkern = 0, epoch = 0;
+  int sts_direct_done = 0;  // the first super-step runs without a graph (loads the kernels)
 
   // CUDA graph of the PCG loop (a WHILE node over chunks of iterations), kept for the
   // last solve's kernels, fields, dt, preconditioner and operator
   cudaGraphExec_t pcg_exec = nullptr;
+  cudaGraph_t pcg_graph = nullptr;     // kept while pcg_exec lives (it owns the conditional handle)
+  cudaStream_t pcg_stream = nullptr;   // the PCG graph's own capture stream
   unsigned long long pcg_key = 0;
   int pcg_kpc = 0;  // kernels per chunk of the cached graph (including the condition kernel)
 

@@ -955,9 +955,12 @@ static int pcg_loop_graph(rkl_ctx *ctx, const PcgFields<T> &f, double dt, int pc
   int rc = RKL_OK;
   if (!ctx->pcg_exec || ctx->pcg_key != key) {
     if (ctx->pcg_exec) cudaGraphExecDestroy(ctx->pcg_exec);
+    if (ctx->pcg_graph) cudaGraphDestroy(ctx->pcg_graph);
+    cudaGetLastError();  // teardown of the previous graph is not an error of this solve
     ctx->pcg_exec = nullptr;
-    if (!ctx->cap_stream &&
-        (rc = cuda_check(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking), "capture stream")))
+    ctx->pcg_graph = nullptr;
+    if (!ctx->pcg_stream &&
+        (rc = cuda_check(ctx, cudaStreamCreateWithFlags(&ctx->pcg_stream, cudaStreamNonBlocking), "capture stream")))
       return rc;
     cudaGraph_t graph = nullptr;
     if ((rc = cuda_check(ctx, cudaGraphCreate(&graph, 0), "PCG graph"))) return rc;
@@ -975,7 +978,7 @@ static int pcg_loop_graph(rkl_ctx *ctx, const PcgFields<T> &f, double dt, int pc
     if (!rc) {
       cudaGraph_t body = np.conditional.phGraph_out[0];
       cudaStream_t user = ctx->stream;
-      ctx->stream = ctx->cap_stream;
+      ctx->stream = ctx->pcg_stream;
       rc = cuda_check(ctx, cudaStreamBeginCaptureToGraph(ctx->stream, body, nullptr, nullptr, 0,
                                                          cudaStreamCaptureModeThreadLocal), "PCG graph capture");
       if (!rc) {
@@ -987,11 +990,13 @@ static int pcg_loop_graph(rkl_ctx *ctx, const PcgFields<T> &f, double dt, int pc
       ctx->stream = user;
     }
     if (!rc) rc = cuda_check(ctx, cudaGraphInstantiate(&ctx->pcg_exec, graph, 0), "PCG graph instantiate");
-    cudaGraphDestroy(graph);
     if (rc) {
+      cudaGraphDestroy(graph);
+      cudaGetLastError();
       ctx->pcg_exec = nullptr;
       return rc;
     }
+    ctx->pcg_graph = graph;
     ctx->pcg_key = key;
     ctx->pcg_kpc = PCG_CHUNK * (pc == RKL_PC_JACOBI ? 3 : 4) + 1;
   }

@@ -327,3 +327,61 @@ def test_superstep_graph_replay_and_invalidation(oracle_mod, R, torch_cuda):
     s = ctx.rkl2_superstep(u, 100.0 * dte, dte)
     assert ctx.kernel_launches - n0 == s  # first stage + s - 1 stages, counted on replay too
     ctx.close()
+
+
+def test_graph_paths_in_a_fresh_process():
+    """In a new process no kernel is loaded yet (lazy module loading): set_coeffs followed by
+    super-steps and a BE solve must work through the graph paths from the start."""
+    import subprocess
+    import sys
+    import textwrap
+
+    code = textwrap.dedent("""
+        import numpy as np, torch
+        from paper_1610_01265_gb300 import rklpcg as R, synth
+        c = synth.conduction_case(16, 12, 24, seed=1)
+        dev = lambda a: torch.from_numpy(np.array(a, dtype=np.float64).ravel()).cuda()
+        ctx = R.Context(c["rf"], 12, 24)
+        dte = ctx.set_conduction(dev(c["T"]), dev(c["bhat"]), dev(c["n"]))
+        outs = []
+        for _ in range(3):
+            u = dev(c["T"])
+            ctx.rkl2_superstep(u, 100 * dte, dte)
+            outs.append(u.cpu().numpy())
+        assert all(np.array_equal(outs[0], o) for o in outs[1:])
+        u = dev(c["T"])
+        code, its, rel = ctx.be_pcg_solve(u, 100 * dte, pc=1, rtol=1e-10, maxit=5000)
+        assert code == 0 and rel[0] <= 1e-10
+        print("fresh ok")
+    """)
+    import os
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0 and "fresh ok" in r.stdout, r.stderr[-2000:]
+
+
+def test_graphs_interleaved_and_teardown(oracle_mod, R, torch_cuda):
+    """Super-steps and graph-driven PCG solves interleaved on one context (each re-capture
+    replaces only its own graph), then a new context after closing it."""
+    O = oracle_mod
+    dims = (16, 12, 24)
+    c = synth.conduction_case(*dims, seed=7)
+    g = O.Grid(c["rf"], dims[1], dims[2])
+    S, W = O.assemble_conduction(g, c["T"], c["bhat"], c["n"])
+    dev = lambda a: torch_cuda.from_numpy(np.array(a, dtype=np.float64)).cuda().view(-1)  # noqa: E731
+    for _ in range(2):
+        ctx = R.Context(c["rf"], dims[1], dims[2])
+        dte = ctx.set_conduction(dev(c["T"]), dev(c["bhat"]), dev(c["n"]))
+        for kind, ratio in (("rkl", 100.0), ("rkl", 1000.0), ("pcg", 100.0), ("rkl", 100.0), ("pcg", 100.0),
+                            ("rkl", 10000.0), ("pcg", 300.0)):
+            u = dev(c["T"])
+            if kind == "rkl":
+                s = ctx.rkl2_superstep(u, ratio * dte, dte)
+                ref = O.rkl2_superstep(g, S, W, c["T"], ratio * dte, s)
+                assert np.linalg.norm(u.cpu().numpy() - ref.ravel()) <= 1e-12 * np.linalg.norm(ref)
+            else:
+                code, its, rel = ctx.be_pcg_solve(u, ratio * dte, pc=1, rtol=1e-10, maxit=5000)
+                x_o, it_o, _, st = O.be_pcg(g, S, W, c["T"], ratio * dte, pc=1, rtol=1e-10)
+                assert code == R.RKL_OK and abs(its[0] - it_o) <= 1
+        ctx.close()
