@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "internal.cuh"
+#include "march.cuh"
 
 namespace rkl {
 
@@ -34,6 +35,20 @@ int ensure_buffer(rkl_ctx *ctx, double **buf, size_t count, const char *what) {
 int ensure_fbuffer(rkl_ctx *ctx, float **buf, size_t count, const char *what) {
   if (*buf) return RKL_OK;
   return cuda_check(ctx, cudaMalloc((void **)buf, count * sizeof(float)), what);
+}
+
+int check_kerr(rkl_ctx *ctx, const int *word) {
+  int v = 0;
+  if (word) {
+    v = *word;
+  } else {
+    int rc = cuda_check(ctx, cudaMemcpy(&v, ctx->d_kerr, sizeof(int), cudaMemcpyDeviceToHost), "error word read");
+    if (rc) return rc;
+  }
+  if (!v) return RKL_OK;
+  int rc = cuda_check(ctx, cudaMemsetAsync(ctx->d_kerr, 0, sizeof(int), ctx->stream), "error word clear");
+  if (rc) return rc;
+  return set_error(ctx, RKL_ECUDA, "a kernel's bounded wait for its asynchronous copies ran out; its outputs hold NaN");
 }
 
 }  // namespace rkl
@@ -149,7 +164,10 @@ int from_device(rkl_ctx *ctx, double *host, const double *dev, size_t n) {
                                          ctx->stream), "device->host copy");
 }
 
-int sync(rkl_ctx *ctx, const char *what) { return cuda_check(ctx, cudaStreamSynchronize(ctx->stream), what); }
+int sync(rkl_ctx *ctx, const char *what) {
+  int rc = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), what);
+  return rc ? rc : check_kerr(ctx, nullptr);
+}
 
 // RKL2 coefficients of Sec. 3 for stage j (b_0 = b_1 = b_2 = 1/3)
 double rkl_b(int j) { return j <= 2 ? 1.0 / 3.0 : ((double)j * j + j - 2.0) / (2.0 * j * (j + 1.0)); }
@@ -222,8 +240,18 @@ int rkl_create(rkl_ctx **out, const rkl_grid *g, int prec, void *stream) {
   }
   if (!rc) rc = cuda_check(ctx, cudaMalloc(&ctx->counter, sizeof(unsigned int)), "alloc counter");
   if (!rc) rc = cuda_check(ctx, cudaMemset(ctx->counter, 0, sizeof(unsigned int)), "clear counter");
-  if (!rc) rc = cuda_check(ctx, cudaMalloc(&ctx->d_state, sizeof(PcgState)), "alloc PCG state");
+  // the PCG state, followed by the kernel error word (set by a bounded wait that ran out)
+  if (!rc) rc = cuda_check(ctx, cudaMalloc(&ctx->d_state, sizeof(PcgState) + 16), "alloc PCG state");
+  if (!rc) {
+    ctx->d_kerr = (int *)(ctx->d_state + 1);
+    rc = cuda_check(ctx, cudaMemset(ctx->d_kerr, 0, sizeof(int)), "clear error word");
+  }
   if (!rc) rc = cuda_check(ctx, cudaMallocHost(&ctx->h_state, sizeof(PcgState) + 64), "alloc pinned state");
+  if (!rc && march_ok(ctx->d.nr)) {  // FP32 conduction kernels fed by bulk copies
+    ctx->march_nchunk = march_chunks(ctx->d.nth, ctx->d.nph, ctx->d.nr, ctx->nsm, ctx->npart);
+    rc = march_setup_stage(ctx);
+    if (!rc) rc = march_setup_spmv(ctx);
+  }
   if (rc) {
     rkl_destroy(ctx);
     return rc;

@@ -158,6 +158,8 @@ struct rkl_ctx {
   double acoef_dt = 0.0;
   double *partials = nullptr;
   int npart = 0;
+  int *d_kerr = nullptr;      // kernel error word, just after the PCG state
+  int march_nchunk = 0;       // phi chunks of the marching FP32 conduction kernels (0: not used)
   unsigned int *counter = nullptr;
   rkl::PcgState *d_state = nullptr;
   rkl::PcgState *h_state = nullptr;  // pinned
@@ -257,6 +259,11 @@ int launch_rkl2_stage_raw(const Dims &d, cudaStream_t stream, const double *coef
                           double mutdt, double gtdt);
 
 int launch_to_float(rkl_ctx *ctx, const double *a, float *b, long long n);
+int march_setup_stage(rkl_ctx *ctx);
+int march_setup_spmv(rkl_ctx *ctx);
+// RKL_ECUDA when a kernel's bounded wait ran out since the last check (the word is
+// cleared); `word` is the value already read back with the PCG state, or nullptr to read it
+int check_kerr(rkl_ctx *ctx, const int *word);
 int launch_rkl2_first_mix(rkl_ctx *ctx, const double *Y0, float *M0f, float *d1, double mut1dt);
 int launch_rkl2_stage_mix(rkl_ctx *ctx, const float *dm1, const float *dm2, const float *M0f,
                           float *dout, double *u, double mu, double nu, double mutdt, double cm0);

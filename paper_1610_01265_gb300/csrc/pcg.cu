@@ -20,6 +20,7 @@
 
 #include "internal.cuh"
 #include "stencil.cuh"
+#include "march.cuh"
 
 namespace rkl {
 
@@ -320,6 +321,51 @@ __global__ void __launch_bounds__(MTHREADS) k_spmv_march(Dims d, const float *__
     double pAp = tot[0];
     st->pAp = pAp;
     if (!(pAp > 0.0) || !isfinite(pAp)) st->status = PCG_BREAKDOWN;
+    else st->alpha = st->rr / pAp;
+  }
+}
+
+// FP32 y = A p = W p + dt S p for symmetric conduction, marching along phi with the planes
+// of p and of the coefficients brought in by bulk copies (march.cuh); per cell the
+// arithmetic of k_spmv<OPK_COND, float>.  alpha = r.z / p.y as in k_spmv.
+struct SpmvEpi {
+  const float *__restrict__ W;
+  float *__restrict__ y;
+  float dt;
+  double dot;
+  float4 w, wn;
+  __device__ __forceinline__ void load(long long c) { wn = *reinterpret_cast<const float4 *>(W + c); }
+  __device__ __forceinline__ void advance() { w = wn; }
+  __device__ __forceinline__ void store(long long c, const float (&s)[4], const float (&pc)[4]) {
+    const float wv[4] = {w.x, w.y, w.z, w.w};
+    float yv[4];
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+      yv[e] = fmaf(wv[e], pc[e], dt * s[e]);
+      dot = fma((double)pc[e], (double)yv[e], dot);
+    }
+    *reinterpret_cast<float4 *>(y + c) = make_float4(yv[0], yv[1], yv[2], yv[3]);
+  }
+  __device__ __forceinline__ void poison(long long c) {
+    const float q = __int_as_float(0x7fc00000);
+    *reinterpret_cast<float4 *>(y + c) = make_float4(q, q, q, q);
+    dot = __longlong_as_double(0x7ff8000000000000LL);
+  }
+};
+
+__global__ void __launch_bounds__(MARCH_THREADS, 1) k_spmv_tma(Dims d, int nchunk, const float *__restrict__ coef,
+                                                              const float *__restrict__ W, float dt,
+                                                              const float *__restrict__ p, float *__restrict__ y,
+                                                              double *partials, unsigned int *counter,
+                                                              PcgState *st, int *kerr) {
+  if (st->status != PCG_RUNNING) return;
+  SpmvEpi e{W, y, dt, 0.0};
+  cond_march32(d, nchunk, coef, p, e, kerr);
+  double v[1] = {e.dot}, tot[1];
+  if (grid_sum<1, MARCH_THREADS>(v, partials, counter, tot) && threadIdx.x == 0) {
+    double pAp = tot[0];
+    st->pAp = pAp;
+    if (!(pAp > 0.0) || !isfinite(pAp) || atomicAdd(kerr, 0) != 0) st->status = PCG_BREAKDOWN;
     else st->alpha = st->rr / pAp;
   }
 }
@@ -677,6 +723,11 @@ __global__ void __launch_bounds__(AB) k_bilu_apply(Dims d, IluPlan pl,
   if (grid_sum<2, AB>(v2, partials, counter, tot) && threadIdx.x == 0) finalize_dots(st, tot[0], tot[1], init != 0);
 }
 
+unsigned int march_grid(const rkl_ctx *ctx) {
+  const int TH = march_th(ctx->d.nr);
+  return (unsigned)(((ctx->d.nth + TH - 1) / TH) * ctx->march_nchunk);
+}
+
 unsigned int stride_grid(const rkl_ctx *ctx) {
   long long g = (ctx->d.N + RB - 1) / RB;
   long long cap = (long long)ctx->nsm * 8;
@@ -684,6 +735,21 @@ unsigned int stride_grid(const rkl_ctx *ctx) {
 }
 
 }  // namespace
+
+// the marching kernels may use up to the opt-in shared memory of a CTA, whatever the
+// grid of the context (the attribute belongs to the kernel, not to a context)
+int march_setup_spmv(rkl_ctx *ctx) {
+  int optin = 0;
+  int rc = cuda_check(ctx, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device),
+                      "shared memory opt-in");
+  if (rc) return rc;
+  if ((size_t)optin < march_smem(ctx->d.nr) + 1024) {
+    ctx->march_nchunk = 0;
+    return RKL_OK;
+  }
+  return cuda_check(ctx, cudaFuncSetAttribute(k_spmv_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - 1024),
+                    "bulk-copy SpMV shared memory");
+}
 
 // Build the wavefront plan of a block shape and (re)factor A = W + dt S when the block
 // shape, dt or the operator changed since the last factorisation.
@@ -817,10 +883,11 @@ static int state_upload(rkl_ctx *ctx, double rtol, int maxit) {
 }
 
 static int state_read(rkl_ctx *ctx) {
-  int rc = cuda_check(ctx, cudaMemcpyAsync(ctx->h_state, ctx->d_state, sizeof(PcgState),
+  int rc = cuda_check(ctx, cudaMemcpyAsync(ctx->h_state, ctx->d_state, sizeof(PcgState) + sizeof(int),
                                            cudaMemcpyDeviceToHost, ctx->stream), "PCG state read");
   if (rc) return rc;
-  return cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "PCG iteration");
+  if ((rc = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "PCG iteration"))) return rc;
+  return check_kerr(ctx, reinterpret_cast<const int *>(ctx->h_state + 1));
 }
 
 static size_t ilu_smem(const rkl_ctx *ctx, size_t elem) {
@@ -849,7 +916,7 @@ static void pcg_first(rkl_ctx *ctx, const PcgFields<T> &f, int pc) {
 struct LoopCfg {
   unsigned g, nblk;
   size_t smem;
-  bool march;
+  bool march, tma;
   dim3 mgrid;
   int kchunk;
 };
@@ -866,7 +933,9 @@ static LoopCfg loop_cfg(const rkl_ctx *ctx, int pc) {
   const int nz = std::max(1, std::min(d.nph, (8 * ctx->nsm + nbx * nby - 1) / (nbx * nby)));
   L.kchunk = (d.nph + nz - 1) / nz;
   L.mgrid = dim3(nbx, nby, (d.nph + L.kchunk - 1) / L.kchunk);
-  L.march = std::is_same<T, float>::value && OP == OPK_COND &&
+  // FP32 symmetric conduction with nr a multiple of 4 up to 256: planes by bulk copies
+  L.tma = std::is_same<T, float>::value && OP == OPK_COND && ctx->march_nchunk > 0;
+  L.march = !L.tma && std::is_same<T, float>::value && OP == OPK_COND &&
             (long long)L.mgrid.x * L.mgrid.y * L.mgrid.z <= (long long)ctx->npart;
   return L;
 }
@@ -881,7 +950,11 @@ static void queue_chunk(rkl_ctx *ctx, const PcgFields<T> &f, double dt, int pc, 
   for (int q = 0; q < chunk; q++) {
     {
       ProfScope prof(ctx, RKL_K_SPMV, q);
-      if (L.march)
+      if (L.tma)
+        k_spmv_tma<<<march_grid(ctx), MARCH_THREADS, march_smem(d.nr), ctx->stream>>>(
+            d, ctx->march_nchunk, (const float *)f.coef, (const float *)f.W, (float)dt, (const float *)f.p,
+            (float *)f.y, ctx->partials, ctx->counter, ctx->d_state, ctx->d_kerr);
+      else if (L.march)
         k_spmv_march<<<L.mgrid, MTHREADS, 0, ctx->stream>>>(d, (const float *)f.coef, (const float *)f.W, (float)dt,
                                                              (const float *)f.p, (float *)f.y, ctx->partials,
                                                              ctx->counter, ctx->d_state, L.kchunk);
@@ -951,6 +1024,7 @@ static int pcg_loop_graph(rkl_ctx *ctx, const PcgFields<T> &f, double dt, int pc
   mix(&L.nblk, sizeof L.nblk);
   mix(&L.smem, sizeof L.smem);
   mix(&L.march, sizeof L.march);
+  mix(&L.tma, sizeof L.tma);
   mix(&L.kchunk, sizeof L.kchunk);
   int rc = RKL_OK;
   if (!ctx->pcg_exec || ctx->pcg_key != key) {

@@ -13,6 +13,7 @@
 
 #include "internal.cuh"
 #include "stencil.cuh"
+#include "march.cuh"
 
 namespace rkl {
 
@@ -121,6 +122,70 @@ __global__ void __launch_bounds__(BLK) k_rkl2_stage_mix(Dims d, const float *__r
   else dout[c] = y;
 }
 
+// The same stage for symmetric conduction, marching along phi with the planes of
+// delta_{j-1} and of the coefficients brought in by bulk copies (march.cuh); per cell
+// the arithmetic of k_rkl2_stage_mix<OPK_COND>.  Yout may alias dm2 (each cell is read
+// by its own thread, a plane ahead of its write).
+struct StageEpi {
+  const float *__restrict__ invW;
+  const float *dm2;
+  const float *__restrict__ M0f;
+  float *dout;
+  double *u;
+  float mu, nu, mutdt, cm0;
+  float4 w, m, z, wn, mn, zn;
+  __device__ __forceinline__ void load(long long c) {
+    wn = *reinterpret_cast<const float4 *>(invW + c);
+    mn = *reinterpret_cast<const float4 *>(M0f + c);
+    zn = dm2 ? *reinterpret_cast<const float4 *>(dm2 + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  __device__ __forceinline__ void advance() {
+    w = wn;
+    m = mn;
+    z = zn;
+  }
+  __device__ __forceinline__ void store(long long c, const float (&s)[4], const float (&uc)[4]) {
+    const float wv[4] = {w.x, w.y, w.z, w.w}, mv[4] = {m.x, m.y, m.z, m.w}, zv[4] = {z.x, z.y, z.z, z.w};
+    float y[4];
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+      const float f = -wv[e] * s[e];
+      float t = mu * uc[e];
+      if (dm2) t = fmaf(nu, zv[e], t);
+      t = fmaf(mutdt, f, t);
+      y[e] = fmaf(cm0, mv[e], t);
+    }
+    if (u) {
+#pragma unroll
+      for (int e = 0; e < 4; e++) u[c + e] += (double)y[e];
+    } else {
+      *reinterpret_cast<float4 *>(dout + c) = make_float4(y[0], y[1], y[2], y[3]);
+    }
+  }
+  __device__ __forceinline__ void poison(long long c) {
+    const float q = __int_as_float(0x7fc00000);
+    if (u) {
+#pragma unroll
+      for (int e = 0; e < 4; e++) u[c + e] = (double)q;
+    } else {
+      *reinterpret_cast<float4 *>(dout + c) = make_float4(q, q, q, q);
+    }
+  }
+};
+
+__global__ void __launch_bounds__(MARCH_THREADS, 1) k_rkl2_stage_mix_tma(Dims d, int nchunk,
+                                                                        const float *__restrict__ coef,
+                                                                        const float *__restrict__ invW,
+                                                                        const float *__restrict__ dm1,
+                                                                        const float *dm2,
+                                                                        const float *__restrict__ M0f,
+                                                                        float *dout, double *u, float mu,
+                                                                        float nu, float mutdt, float cm0,
+                                                                        int *kerr) {
+  StageEpi e{invW, dm2, M0f, dout, u, mu, nu, mutdt, cm0};
+  cond_march32(d, nchunk, coef, dm1, e, kerr);
+}
+
 __global__ void __launch_bounds__(BLK) k_to_float(long long n, const double *__restrict__ a,
                                                   float *__restrict__ b) {
   for (long long c = (long long)blockIdx.x * BLK + threadIdx.x; c < n; c += (long long)gridDim.x * BLK)
@@ -128,6 +193,20 @@ __global__ void __launch_bounds__(BLK) k_to_float(long long n, const double *__r
 }
 
 }  // namespace
+
+int march_setup_stage(rkl_ctx *ctx) {
+  int optin = 0;
+  int rc = cuda_check(ctx, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device),
+                      "shared memory opt-in");
+  if (rc) return rc;
+  if ((size_t)optin < march_smem(ctx->d.nr) + 1024) {
+    ctx->march_nchunk = 0;
+    return RKL_OK;
+  }
+  return cuda_check(ctx, cudaFuncSetAttribute(k_rkl2_stage_mix_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              optin - 1024),
+                    "bulk-copy stage shared memory");
+}
 
 int launch_to_float(rkl_ctx *ctx, const double *a, float *b, long long n) {
   long long g = std::min<long long>((n + BLK - 1) / BLK, (long long)ctx->nsm * 16);
@@ -150,6 +229,15 @@ int launch_rkl2_first_mix(rkl_ctx *ctx, const double *Y0, float *M0f, float *d1,
 int launch_rkl2_stage_mix(rkl_ctx *ctx, const float *dm1, const float *dm2, const float *M0f,
                           float *dout, double *u, double mu, double nu, double mutdt, double cm0) {
   ProfScope prof(ctx, RKL_K_RKL2_STAGE);
+  if (ctx->op == OPK_COND && ctx->march_nchunk > 0) {
+    const int TH = march_th(ctx->d.nr);
+    const unsigned grid = (unsigned)(((ctx->d.nth + TH - 1) / TH) * ctx->march_nchunk);
+    k_rkl2_stage_mix_tma<<<grid, MARCH_THREADS, march_smem(ctx->d.nr), ctx->stream>>>(
+        ctx->d, ctx->march_nchunk, ctx->coef32, ctx->invW32, dm1, dm2, M0f, dout, u, (float)mu, (float)nu,
+        (float)mutdt, (float)cm0, ctx->d_kerr);
+    ctx->launches += 1;
+    return cuda_check(ctx, cudaGetLastError(), "mixed rkl2 stage launch");
+  }
   // a block of 256 threads: the whole (padded) r line when it is short, several theta rows
   const unsigned bx = (unsigned)std::min(256, ((ctx->d.nr + 31) / 32) * 32), by = 256 / bx;
   const dim3 block(bx, by), grid(grid_for(ctx->d.nr, bx), grid_for(ctx->d.nth, by), (unsigned)ctx->d.nph);

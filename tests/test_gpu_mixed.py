@@ -33,8 +33,14 @@ def dev(a):
     return torch.from_numpy(np.array(a, dtype=np.float64)).cuda()
 
 
-# (37, 11, 13): ragged against the 32 x 8 tiles and the phi chunks of the marching kernels
-@pytest.mark.parametrize("dims", [(16, 12, 24), (32, 32, 64), (37, 11, 13)])
+# nr a multiple of 4 up to 256 runs the phi-marching kernels fed by bulk copies: (128, 20,
+# 9), (256, 10, 7) and (32, 70, 5) have several theta tiles with halo rows on both sides,
+# (128, 40, 96) phi chunks long enough for the steady refill of the copy rings, (36, 11,
+# 13), (132, 6, 8) and (8, 5, 6) tiles with idle threads; (37, 11, 13) and (260, 6, 4) run
+# the one-cell-per-thread kernels
+@pytest.mark.parametrize("dims", [(16, 12, 24), (32, 32, 64), (36, 11, 13), (132, 6, 8), (8, 5, 6),
+                                  (128, 20, 9), (256, 10, 7), (32, 70, 5), (128, 40, 96), (37, 11, 13),
+                                  (260, 6, 4)])
 @pytest.mark.parametrize("ratio", [100.0, 1000.0, 10000.0])
 def test_mixed_rkl2_conduction(oracle_mod, R, dims, ratio):
     O = oracle_mod
@@ -73,15 +79,20 @@ def test_mixed_rkl2_viscosity(oracle_mod, R):
     ctx.close()
 
 
-# (37, 11, 13) is ragged against the tiles of the FP32 SpMV; block ILU0 on its thin
-# (37, 11, 1) blocks is a weaker preconditioner than Jacobi there (1161 vs 703 FP64
-# iterations at 1e4 dt_exp), so that case runs at 100 dt_exp
+# (37, 11, 13) runs the one-cell-per-thread FP32 SpMV, the others the phi-marching one fed
+# by bulk copies ((36, 11, 13) and (132, 6, 8) with idle threads, (128, 40, 96) with
+# several theta tiles and longer phi chunks); block ILU0 on thin (nr, nth, 1) blocks is a
+# weaker preconditioner than Jacobi (1161 vs 703 FP64 iterations at 1e4 dt_exp on
+# 37 x 11 x 13), so those cases run at 100 dt_exp
 @pytest.mark.parametrize("pc,ratio,dims", [(1, 100.0, (32, 32, 64)), (2, 100.0, (32, 32, 64)),
                                            (1, 10000.0, (32, 32, 64)), (2, 10000.0, (32, 32, 64)),
-                                           (1, 10000.0, (37, 11, 13)), (2, 100.0, (37, 11, 13))])
+                                           (1, 10000.0, (37, 11, 13)), (2, 100.0, (37, 11, 13)),
+                                           (1, 10000.0, (36, 11, 13)), (2, 100.0, (36, 11, 13)),
+                                           (1, 1000.0, (132, 6, 8)), (1, 1000.0, (128, 40, 96)),
+                                           (2, 1000.0, (128, 40, 96))])
 def test_mixed_be_meets_fp64_residual(oracle_mod, R, pc, ratio, dims):
     O = oracle_mod
-    block = (8, 8, 8) if dims[0] % 8 == 0 else (37, 11, 1)
+    block = (8, 8, 8) if all(n % 8 == 0 for n in dims) else (dims[0], dims[1], 1)
     c = synth.conduction_case(*dims, seed=3)
     g = O.Grid(c["rf"], dims[1], dims[2])
     S, W = O.assemble_conduction(g, c["T"], c["bhat"], c["n"])
