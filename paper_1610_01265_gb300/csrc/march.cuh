@@ -86,7 +86,8 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
 __device__ __forceinline__ float4 lds4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
 
 // a row of u around the four cells: x[0] = u(i0-1), x[1..4] = u(i0..i0+3), x[5] = u(i0+4);
-// a missing r neighbour is clamped onto the cell itself, as in neighbours()
+// a missing r neighbour is clamped onto the cell itself, as in neighbours().  (Taking
+// the neighbours from the adjacent lanes by shuffles instead was slower.)
 __device__ __forceinline__ void row6(const float *row, int i0, int nr, float (&x)[6]) {
   const float4 v = lds4(row + i0);
   x[1] = v.x;
