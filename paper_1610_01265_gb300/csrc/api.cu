@@ -248,7 +248,12 @@ int rkl_create(rkl_ctx **out, const rkl_grid *g, int prec, void *stream) {
   }
   if (!rc) rc = cuda_check(ctx, cudaMallocHost(&ctx->h_state, sizeof(PcgState) + 64), "alloc pinned state");
   if (!rc && march_ok(ctx->d.nr)) {  // FP32 conduction kernels fed by bulk copies
-    ctx->march_nchunk = march_chunks(ctx->d.nth, ctx->d.nph, ctx->d.nr, ctx->nsm, ctx->npart);
+    int smem_sm = 0;
+    rc = cuda_check(ctx, cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, ctx->device),
+                    "shared memory per SM");
+    if (!rc) ctx->march_nchunk = march_chunks(ctx->d.nth, ctx->d.nph, ctx->d.nr, ctx->nsm, smem_sm, ctx->npart);
+  }
+  if (!rc && ctx->march_nchunk > 0) {
     rc = march_setup_stage(ctx);
     if (!rc) rc = march_setup_spmv(ctx);
   }

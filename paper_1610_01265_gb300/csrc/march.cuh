@@ -2,9 +2,9 @@
 // shared memory by bulk asynchronous copies (the TMA engine, cp.async.bulk) that signal
 // mbarriers.
 //
-// A CTA of 256 threads owns a tile of TH = 256 / (nr/4) theta rows (all nr cells of each
-// row, four consecutive r cells per thread) and a chunk [k0, k1) of phi planes.  For
-// each plane it holds in shared memory
+// A CTA owns a tile of TH theta rows (all nr cells of each row, four consecutive r cells
+// per thread; march_th below) and a chunk [k0, k1) of phi planes.  For each plane it
+// holds in shared memory
 //   u     rows j0-1 .. j0+TH: the tile and its theta halo          ring of MU = 5 planes
 //   coef  the 10 slots of the tile's own rows, plus the halo rows
 //         slots 1, 3, 4, 8 of row j0-1 and slot 7 of row j0+th     ring of MC = 4 planes
@@ -27,18 +27,24 @@
 //
 // Per cell, the products and the order of the sums are those of S_apply_cond.
 #pragma once
+#include <algorithm>
 #include <cstdint>
 
 #include "internal.cuh"
 
 namespace rkl {
 
-constexpr int MARCH_THREADS = 256, MARCH_MU = 5, MARCH_MC = 4, MARCH_NB = 3;
+constexpr int MARCH_MAX_THREADS = 256, MARCH_MU = 5, MARCH_MC = 4, MARCH_NB = 3;
 constexpr long long MARCH_WAIT_CYCLES = 4000000000LL;  // ~2 s at the maximum SM clock
 
 // the marching kernels take grids with nr a multiple of 4 and at most 256
 __host__ __device__ inline bool march_ok(int nr) { return nr % 4 == 0 && nr >= 4 && nr <= 256; }
-__host__ __device__ inline int march_th(int nr) { return MARCH_THREADS / (nr / 4); }
+// theta rows per tile: at least 4 (halo rows cost 2 per tile) and at least 512 cells per
+// plane; a CTA has one thread per four cells of a tile plane, rounded up to whole warps,
+// so tiles of nr <= 128 take 128 threads and about 108 KB (two CTAs per SM), tiles of
+// nr = 256 take 256 threads and about 215 KB
+__host__ __device__ inline int march_th(int nr) { return 128 / (nr / 4) > 4 ? 128 / (nr / 4) : 4; }
+__host__ __device__ inline int march_threads(int nr) { return ((nr / 4) * march_th(nr) + 31) / 32 * 32; }
 __host__ __device__ inline size_t march_smem(int nr) {
   const int TH = march_th(nr);
   return sizeof(float) * ((size_t)MARCH_MU * (TH + 2) * nr + (size_t)MARCH_MC * (10 * TH + 5) * nr);
@@ -133,7 +139,7 @@ __device__ __forceinline__ bool cond_march32(const Dims &d, int nchunk, const fl
                                              const float *__restrict__ u, Epi &epi, int *kerr) {
   extern __shared__ __align__(16) float msm[];
   __shared__ __align__(8) uint64_t bars[MARCH_NB];
-  const int nr = d.nr, nth = d.nth, nph = d.nph, nq = nr >> 2, TH = MARCH_THREADS / nq;
+  const int nr = d.nr, nth = d.nth, nph = d.nph, nq = nr >> 2, TH = march_th(nr);
   const int ntile = (nth + TH - 1) / TH;
   const int tile = (int)(blockIdx.x % (unsigned)ntile), chunk = (int)(blockIdx.x / (unsigned)ntile);
   const int j0 = tile * TH, th = min(TH, nth - j0);
@@ -283,15 +289,16 @@ __device__ __forceinline__ bool cond_march32(const Dims &d, int nchunk, const fl
   return false;
 }
 
-// phi chunks per theta tile: the fewest waves of one CTA per SM, each item paying
-// about two planes of prologue
-inline int march_chunks(int nth, int nph, int nr, int nsm, int max_items) {
+// phi chunks per theta tile: the fewest waves of resident CTAs (as many per SM as its
+// shared memory holds), each item paying about two planes of prologue
+inline int march_chunks(int nth, int nph, int nr, int nsm, int smem_per_sm, int max_items) {
   const int TH = march_th(nr), ntile = (nth + TH - 1) / TH;
+  const long long slots = (long long)nsm * std::max<long long>(1, smem_per_sm / (long long)(march_smem(nr) + 1024));
   int best = 1;
   double best_cost = 1e300;
   for (int n = 1; n <= nph && (long long)n * ntile <= max_items; n++) {
     const long long items = (long long)n * ntile;
-    const double cost = (double)((items + nsm - 1) / nsm) * ((double)nph / n + 2.0);
+    const double cost = (double)((items + slots - 1) / slots) * ((double)nph / n + 2.0);
     if (cost < best_cost - 1e-9) {
       best_cost = cost;
       best = n;

@@ -34,9 +34,10 @@ __device__ __forceinline__ int slot_dj(int s) { return s == 0 ? 0 : (s < 10 ? -f
 __device__ __forceinline__ int slot_dk(int s) { return s == 0 ? 0 : (s < 10 ? -fwd_dk(s - 1) : fwd_dk(s - 10)); }
 
 // Sum NV per-thread values over the whole grid.  Returns true (in every thread of the
-// last block to finish) with the totals in tot[] of thread 0.  Blocks must be 1-D with
-// exactly BS threads (threadIdx.x is the thread's rank; one counter increment per block);
-// bid / nb are the block's linear index and the number of blocks.
+// last block to finish) with the totals in tot[] of thread 0.  Blocks must be 1-D with a
+// multiple of 32 threads, at most BS (threadIdx.x is the thread's rank; one counter
+// increment per block); bid / nb are the block's linear index and the number of blocks.
+// The order of the sums depends only on the launch shape, so the result is reproducible.
 template <int NV, int BS>
 __device__ bool grid_sum(double (&v)[NV], double *partials, unsigned int *counter,
                          double (&tot)[NV], unsigned int bid, unsigned int nb) {
@@ -54,7 +55,7 @@ __device__ bool grid_sum(double (&v)[NV], double *partials, unsigned int *counte
 #pragma unroll
     for (int q = 0; q < NV; q++) {
       double s = 0.0;
-      for (int w = 0; w < BS / 32; w++) s += sh[q][w];
+      for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += sh[q][w];
       partials[(size_t)bid * NV + q] = s;
     }
     __threadfence();
@@ -67,7 +68,7 @@ __device__ bool grid_sum(double (&v)[NV], double *partials, unsigned int *counte
 #pragma unroll
   for (int q = 0; q < NV; q++) {
     double s = 0.0;
-    for (unsigned int b = threadIdx.x; b < nb; b += BS) s += __ldcg(&partials[(size_t)b * NV + q]);
+    for (unsigned int b = threadIdx.x; b < nb; b += blockDim.x) s += __ldcg(&partials[(size_t)b * NV + q]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
     if (lane == 0) sh[q][warp] = s;
@@ -77,7 +78,7 @@ __device__ bool grid_sum(double (&v)[NV], double *partials, unsigned int *counte
 #pragma unroll
     for (int q = 0; q < NV; q++) {
       double s = 0.0;
-      for (int w = 0; w < BS / 32; w++) s += sh[q][w];
+      for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += sh[q][w];
       tot[q] = s;
     }
     *counter = 0u;
@@ -353,7 +354,7 @@ struct SpmvEpi {
   }
 };
 
-__global__ void __launch_bounds__(MARCH_THREADS, 1) k_spmv_tma(Dims d, int nchunk, const float *__restrict__ coef,
+__global__ void __launch_bounds__(MARCH_MAX_THREADS, 1) k_spmv_tma(Dims d, int nchunk, const float *__restrict__ coef,
                                                               const float *__restrict__ W, float dt,
                                                               const float *__restrict__ p, float *__restrict__ y,
                                                               double *partials, unsigned int *counter,
@@ -362,7 +363,7 @@ __global__ void __launch_bounds__(MARCH_THREADS, 1) k_spmv_tma(Dims d, int nchun
   SpmvEpi e{W, y, dt, 0.0};
   cond_march32(d, nchunk, coef, p, e, kerr);
   double v[1] = {e.dot}, tot[1];
-  if (grid_sum<1, MARCH_THREADS>(v, partials, counter, tot) && threadIdx.x == 0) {
+  if (grid_sum<1, MARCH_MAX_THREADS>(v, partials, counter, tot) && threadIdx.x == 0) {
     double pAp = tot[0];
     st->pAp = pAp;
     if (!(pAp > 0.0) || !isfinite(pAp) || atomicAdd(kerr, 0) != 0) st->status = PCG_BREAKDOWN;
@@ -951,7 +952,7 @@ static void queue_chunk(rkl_ctx *ctx, const PcgFields<T> &f, double dt, int pc, 
     {
       ProfScope prof(ctx, RKL_K_SPMV, q);
       if (L.tma)
-        k_spmv_tma<<<march_grid(ctx), MARCH_THREADS, march_smem(d.nr), ctx->stream>>>(
+        k_spmv_tma<<<march_grid(ctx), march_threads(d.nr), march_smem(d.nr), ctx->stream>>>(
             d, ctx->march_nchunk, (const float *)f.coef, (const float *)f.W, (float)dt, (const float *)f.p,
             (float *)f.y, ctx->partials, ctx->counter, ctx->d_state, ctx->d_kerr);
       else if (L.march)

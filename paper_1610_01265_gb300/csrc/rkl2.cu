@@ -173,7 +173,7 @@ struct StageEpi {
   }
 };
 
-__global__ void __launch_bounds__(MARCH_THREADS, 1) k_rkl2_stage_mix_tma(Dims d, int nchunk,
+__global__ void __launch_bounds__(MARCH_MAX_THREADS, 1) k_rkl2_stage_mix_tma(Dims d, int nchunk,
                                                                         const float *__restrict__ coef,
                                                                         const float *__restrict__ invW,
                                                                         const float *__restrict__ dm1,
@@ -232,7 +232,7 @@ int launch_rkl2_stage_mix(rkl_ctx *ctx, const float *dm1, const float *dm2, cons
   if (ctx->op == OPK_COND && ctx->march_nchunk > 0) {
     const int TH = march_th(ctx->d.nr);
     const unsigned grid = (unsigned)(((ctx->d.nth + TH - 1) / TH) * ctx->march_nchunk);
-    k_rkl2_stage_mix_tma<<<grid, MARCH_THREADS, march_smem(ctx->d.nr), ctx->stream>>>(
+    k_rkl2_stage_mix_tma<<<grid, march_threads(ctx->d.nr), march_smem(ctx->d.nr), ctx->stream>>>(
         ctx->d, ctx->march_nchunk, ctx->coef32, ctx->invW32, dm1, dm2, M0f, dout, u, (float)mu, (float)nu,
         (float)mutdt, (float)cm0, ctx->d_kerr);
     ctx->launches += 1;
