@@ -77,7 +77,7 @@ def parse_args():
     p.add_argument("--warmstart", action="store_true",
                    help="run the learned-initial-guess study (200 BE steps with heating) instead of the step")
     p.add_argument("--profile", choices=("stage", "apply", "pcg-jacobi", "pcg-bilu0", "setup", "stage-mix",
-                                         "pcg-jacobi-mix", "ws-forward", "ws-train"),
+                                         "pcg-jacobi-mix", "pcg-bilu0-mix", "ws-forward", "ws-train"),
                    help="run only a minimal case of one kernel family for an ncu capture (no timing)")
     return p.parse_args()
 
@@ -623,7 +623,7 @@ def profile_case(args):
             ctx.apply_F(T, F)
     elif args.profile in ("pcg-jacobi", "pcg-jacobi-mix"):
         ctx.be_pcg_solve(u, 100 * dte, pc=R.RKL_PC_JACOBI, rtol=0.0, maxit=3)
-    elif args.profile == "pcg-bilu0":
+    elif args.profile in ("pcg-bilu0", "pcg-bilu0-mix"):
         ctx.be_pcg_solve(u, 100 * dte, pc=R.RKL_PC_BILU0, block=BLOCK, rtol=0.0, maxit=3)
     elif args.profile == "setup":
         ctx.set_conduction(T, b, n, beta_tcut=BETA_TCUT)
