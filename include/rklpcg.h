@@ -31,8 +31,13 @@
  * aborts or throws across the ABI.  rkl_strerror() names a code and
  * rkl_last_error() gives the context's last detailed message.  Device-side failures
  * (non-finite inputs, CG breakdown, non-convergence) are reported through a status
- * word written by the kernels, never by trapping the GPU.  A context is not
- * thread-safe: one host thread at a time.
+ * word written by the kernels, never by trapping the GPU.  The FP32 kernels that stream
+ * planes through bulk asynchronous copies wait for them with a time limit (about two
+ * seconds); a wait that runs out (a device fault, never an ordinary outcome) writes NaN
+ * over the outputs of that kernel and sets an error word, and the next call that
+ * synchronises with the device (a PCG state read, or the end of a call on host arrays)
+ * returns RKL_ECUDA and clears it.  A context is not thread-safe: one host thread at a
+ * time.
  */
 #ifndef RKLPCG_H
 #define RKLPCG_H
