@@ -251,9 +251,10 @@ int rkl_create(rkl_ctx **out, const rkl_grid *g, int prec, void *stream) {
     int smem_sm = 0;
     rc = cuda_check(ctx, cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, ctx->device),
                     "shared memory per SM");
-    if (!rc) ctx->march_nchunk = march_chunks(ctx->d.nth, ctx->d.nph, ctx->d.nr, ctx->nsm, smem_sm, ctx->npart);
+    for (int op = OPK_COND; !rc && op <= OPK_VISC; op++)
+      ctx->march_nchunk[op] = march_chunks(ctx->d.nth, ctx->d.nph, ctx->d.nr, op, ctx->nsm, smem_sm, ctx->npart);
   }
-  if (!rc && ctx->march_nchunk > 0) {
+  if (!rc && march_ok(ctx->d.nr)) {
     rc = march_setup_stage(ctx);
     if (!rc) rc = march_setup_spmv(ctx);
   }

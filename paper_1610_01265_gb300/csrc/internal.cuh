@@ -159,7 +159,7 @@ struct rkl_ctx {
   double *partials = nullptr;
   int npart = 0;
   int *d_kerr = nullptr;      // kernel error word, just after the PCG state
-  int march_nchunk = 0;       // phi chunks of the marching FP32 conduction kernels (0: not used)
+  int march_nchunk[2] = {0, 0};  // phi chunks of the marching FP32 kernels per operator (0: not used)
   unsigned int *counter = nullptr;
   rkl::PcgState *d_state = nullptr;
   rkl::PcgState *h_state = nullptr;  // pinned

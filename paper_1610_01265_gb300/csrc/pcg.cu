@@ -326,9 +326,9 @@ __global__ void __launch_bounds__(MTHREADS) k_spmv_march(Dims d, const float *__
   }
 }
 
-// FP32 y = A p = W p + dt S p for symmetric conduction, marching along phi with the planes
-// of p and of the coefficients brought in by bulk copies (march.cuh); per cell the
-// arithmetic of k_spmv<OPK_COND, float>.  alpha = r.z / p.y as in k_spmv.
+// FP32 y = A p = W p + dt S p for symmetric conduction and viscosity, marching along phi
+// with the planes of p and of the coefficients brought in by bulk copies (march.cuh); per
+// cell the arithmetic of k_spmv<OP, float>.  alpha = r.z / p.y as in k_spmv.
 struct SpmvEpi {
   const float *__restrict__ W;
   float *__restrict__ y;
@@ -354,6 +354,7 @@ struct SpmvEpi {
   }
 };
 
+template <int OP>
 __global__ void __launch_bounds__(MARCH_MAX_THREADS, 1) k_spmv_tma(Dims d, int nchunk, const float *__restrict__ coef,
                                                               const float *__restrict__ W, float dt,
                                                               const float *__restrict__ p, float *__restrict__ y,
@@ -361,7 +362,7 @@ __global__ void __launch_bounds__(MARCH_MAX_THREADS, 1) k_spmv_tma(Dims d, int n
                                                               PcgState *st, int *kerr) {
   if (st->status != PCG_RUNNING) return;
   SpmvEpi e{W, y, dt, 0.0};
-  cond_march32(d, nchunk, coef, p, e, kerr);
+  march32<OP>(d, nchunk, coef, p, e, kerr);
   double v[1] = {e.dot}, tot[1];
   if (grid_sum<1, MARCH_MAX_THREADS>(v, partials, counter, tot) && threadIdx.x == 0) {
     double pAp = tot[0];
@@ -724,9 +725,9 @@ __global__ void __launch_bounds__(AB) k_bilu_apply(Dims d, IluPlan pl,
   if (grid_sum<2, AB>(v2, partials, counter, tot) && threadIdx.x == 0) finalize_dots(st, tot[0], tot[1], init != 0);
 }
 
-unsigned int march_grid(const rkl_ctx *ctx) {
+unsigned int march_grid(const rkl_ctx *ctx, int op) {
   const int TH = march_th(ctx->d.nr);
-  return (unsigned)(((ctx->d.nth + TH - 1) / TH) * ctx->march_nchunk);
+  return (unsigned)(((ctx->d.nth + TH - 1) / TH) * ctx->march_nchunk[op]);
 }
 
 unsigned int stride_grid(const rkl_ctx *ctx) {
@@ -744,11 +745,14 @@ int march_setup_spmv(rkl_ctx *ctx) {
   int rc = cuda_check(ctx, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device),
                       "shared memory opt-in");
   if (rc) return rc;
-  if ((size_t)optin < march_smem(ctx->d.nr) + 1024) {
-    ctx->march_nchunk = 0;
-    return RKL_OK;
-  }
-  return cuda_check(ctx, cudaFuncSetAttribute(k_spmv_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - 1024),
+  for (int op = OPK_COND; op <= OPK_VISC; op++)
+    if ((size_t)optin < march_smem(ctx->d.nr, op) + 1024) ctx->march_nchunk[op] = 0;
+  rc = cuda_check(ctx, cudaFuncSetAttribute(k_spmv_tma<OPK_COND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            optin - 1024),
+                  "bulk-copy SpMV shared memory");
+  if (rc) return rc;
+  return cuda_check(ctx, cudaFuncSetAttribute(k_spmv_tma<OPK_VISC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              optin - 1024),
                     "bulk-copy SpMV shared memory");
 }
 
@@ -934,11 +938,23 @@ static LoopCfg loop_cfg(const rkl_ctx *ctx, int pc) {
   const int nz = std::max(1, std::min(d.nph, (8 * ctx->nsm + nbx * nby - 1) / (nbx * nby)));
   L.kchunk = (d.nph + nz - 1) / nz;
   L.mgrid = dim3(nbx, nby, (d.nph + L.kchunk - 1) / L.kchunk);
-  // FP32 symmetric conduction with nr a multiple of 4 up to 256: planes by bulk copies
-  L.tma = std::is_same<T, float>::value && OP == OPK_COND && ctx->march_nchunk > 0;
+  // FP32 symmetric conduction or viscosity with nr a multiple of 4 up to 256: planes by
+  // bulk copies
+  L.tma = std::is_same<T, float>::value && (OP == OPK_COND || OP == OPK_VISC) && ctx->march_nchunk[OP] > 0;
   L.march = !L.tma && std::is_same<T, float>::value && OP == OPK_COND &&
             (long long)L.mgrid.x * L.mgrid.y * L.mgrid.z <= (long long)ctx->npart;
   return L;
+}
+
+// FP32 y = A p through the bulk-copy marching kernel (loop_cfg decides when it applies)
+template <int OP, typename T>
+static void launch_spmv_tma(rkl_ctx *ctx, const PcgFields<T> &f, double dt) {
+  if constexpr ((OP == OPK_COND || OP == OPK_VISC) && std::is_same<T, float>::value) {
+    const Dims &d = ctx->d;
+    k_spmv_tma<OP><<<march_grid(ctx, OP), march_threads(d.nr), march_smem(d.nr, OP), ctx->stream>>>(
+        d, ctx->march_nchunk[OP], f.coef, f.W, (float)dt, f.p, f.y, ctx->partials, ctx->counter, ctx->d_state,
+        ctx->d_kerr);
+  }
 }
 
 // `chunk` iterations of Fig. 1 on ctx->stream; every kernel returns at once when the
@@ -952,9 +968,7 @@ static void queue_chunk(rkl_ctx *ctx, const PcgFields<T> &f, double dt, int pc, 
     {
       ProfScope prof(ctx, RKL_K_SPMV, q);
       if (L.tma)
-        k_spmv_tma<<<march_grid(ctx), march_threads(d.nr), march_smem(d.nr), ctx->stream>>>(
-            d, ctx->march_nchunk, (const float *)f.coef, (const float *)f.W, (float)dt, (const float *)f.p,
-            (float *)f.y, ctx->partials, ctx->counter, ctx->d_state, ctx->d_kerr);
+        launch_spmv_tma<OP, T>(ctx, f, dt);
       else if (L.march)
         k_spmv_march<<<L.mgrid, MTHREADS, 0, ctx->stream>>>(d, (const float *)f.coef, (const float *)f.W, (float)dt,
                                                              (const float *)f.p, (float *)f.y, ctx->partials,

@@ -122,9 +122,9 @@ __global__ void __launch_bounds__(BLK) k_rkl2_stage_mix(Dims d, const float *__r
   else dout[c] = y;
 }
 
-// The same stage for symmetric conduction, marching along phi with the planes of
-// delta_{j-1} and of the coefficients brought in by bulk copies (march.cuh); per cell
-// the arithmetic of k_rkl2_stage_mix<OPK_COND>.  Yout may alias dm2 (each cell is read
+// The same stage for symmetric conduction and viscosity, marching along phi with the
+// planes of delta_{j-1} and of the coefficients brought in by bulk copies (march.cuh);
+// per cell the arithmetic of k_rkl2_stage_mix<OP>.  Yout may alias dm2 (each cell is read
 // by its own thread, a plane ahead of its write).
 struct StageEpi {
   const float *__restrict__ invW;
@@ -173,6 +173,7 @@ struct StageEpi {
   }
 };
 
+template <int OP>
 __global__ void __launch_bounds__(MARCH_MAX_THREADS, 1) k_rkl2_stage_mix_tma(Dims d, int nchunk,
                                                                         const float *__restrict__ coef,
                                                                         const float *__restrict__ invW,
@@ -183,7 +184,7 @@ __global__ void __launch_bounds__(MARCH_MAX_THREADS, 1) k_rkl2_stage_mix_tma(Dim
                                                                         float nu, float mutdt, float cm0,
                                                                         int *kerr) {
   StageEpi e{invW, dm2, M0f, dout, u, mu, nu, mutdt, cm0};
-  cond_march32(d, nchunk, coef, dm1, e, kerr);
+  march32<OP>(d, nchunk, coef, dm1, e, kerr);
 }
 
 __global__ void __launch_bounds__(BLK) k_to_float(long long n, const double *__restrict__ a,
@@ -199,12 +200,14 @@ int march_setup_stage(rkl_ctx *ctx) {
   int rc = cuda_check(ctx, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device),
                       "shared memory opt-in");
   if (rc) return rc;
-  if ((size_t)optin < march_smem(ctx->d.nr) + 1024) {
-    ctx->march_nchunk = 0;
-    return RKL_OK;
-  }
-  return cuda_check(ctx, cudaFuncSetAttribute(k_rkl2_stage_mix_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              optin - 1024),
+  for (int op = OPK_COND; op <= OPK_VISC; op++)
+    if ((size_t)optin < march_smem(ctx->d.nr, op) + 1024) ctx->march_nchunk[op] = 0;
+  rc = cuda_check(ctx, cudaFuncSetAttribute(k_rkl2_stage_mix_tma<OPK_COND>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, optin - 1024),
+                  "bulk-copy stage shared memory");
+  if (rc) return rc;
+  return cuda_check(ctx, cudaFuncSetAttribute(k_rkl2_stage_mix_tma<OPK_VISC>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, optin - 1024),
                     "bulk-copy stage shared memory");
 }
 
@@ -229,12 +232,18 @@ int launch_rkl2_first_mix(rkl_ctx *ctx, const double *Y0, float *M0f, float *d1,
 int launch_rkl2_stage_mix(rkl_ctx *ctx, const float *dm1, const float *dm2, const float *M0f,
                           float *dout, double *u, double mu, double nu, double mutdt, double cm0) {
   ProfScope prof(ctx, RKL_K_RKL2_STAGE);
-  if (ctx->op == OPK_COND && ctx->march_nchunk > 0) {
-    const int TH = march_th(ctx->d.nr);
-    const unsigned grid = (unsigned)(((ctx->d.nth + TH - 1) / TH) * ctx->march_nchunk);
-    k_rkl2_stage_mix_tma<<<grid, march_threads(ctx->d.nr), march_smem(ctx->d.nr), ctx->stream>>>(
-        ctx->d, ctx->march_nchunk, ctx->coef32, ctx->invW32, dm1, dm2, M0f, dout, u, (float)mu, (float)nu,
-        (float)mutdt, (float)cm0, ctx->d_kerr);
+  if ((ctx->op == OPK_COND || ctx->op == OPK_VISC) && ctx->march_nchunk[ctx->op] > 0) {
+    const int TH = march_th(ctx->d.nr), nchunk = ctx->march_nchunk[ctx->op];
+    const unsigned grid = (unsigned)(((ctx->d.nth + TH - 1) / TH) * nchunk);
+    const dim3 block(march_threads(ctx->d.nr));
+    if (ctx->op == OPK_COND)
+      k_rkl2_stage_mix_tma<OPK_COND><<<grid, block, march_smem(ctx->d.nr, OPK_COND), ctx->stream>>>(
+          ctx->d, nchunk, ctx->coef32, ctx->invW32, dm1, dm2, M0f, dout, u, (float)mu, (float)nu, (float)mutdt,
+          (float)cm0, ctx->d_kerr);
+    else
+      k_rkl2_stage_mix_tma<OPK_VISC><<<grid, block, march_smem(ctx->d.nr, OPK_VISC), ctx->stream>>>(
+          ctx->d, nchunk, ctx->coef32, ctx->invW32, dm1, dm2, M0f, dout, u, (float)mu, (float)nu, (float)mutdt,
+          (float)cm0, ctx->d_kerr);
     ctx->launches += 1;
     return cuda_check(ctx, cudaGetLastError(), "mixed rkl2 stage launch");
   }

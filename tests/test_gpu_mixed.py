@@ -62,9 +62,11 @@ def test_mixed_rkl2_conduction(oracle_mod, R, dims, ratio):
     ctx.close()
 
 
-def test_mixed_rkl2_viscosity(oracle_mod, R):
+# viscosity through the phi-marching bulk-copy kernels ((128, 20, 9), (256, 10, 7): several
+# theta tiles; (36, 11, 13): idle threads) and the one-cell-per-thread ones ((37, 11, 13))
+@pytest.mark.parametrize("dims", [(16, 12, 24), (128, 20, 9), (256, 10, 7), (36, 11, 13), (37, 11, 13)])
+def test_mixed_rkl2_viscosity(oracle_mod, R, dims):
     O = oracle_mod
-    dims = (16, 12, 24)
     v = synth.viscosity_case(*dims, seed=2)
     g = O.Grid(v["rf"], dims[1], dims[2])
     S, W = O.assemble_viscosity(g, v["rho"], v["nu"])
@@ -110,16 +112,17 @@ def test_mixed_be_meets_fp64_residual(oracle_mod, R, pc, ratio, dims):
     ctx.close()
 
 
-def test_mixed_be_viscosity_three_components(oracle_mod, R):
+@pytest.mark.parametrize("pc,dims,block", [(2, (16, 12, 24), (4, 4, 4)), (1, (128, 20, 16), (8, 4, 8)),
+                                           (2, (128, 20, 16), (8, 4, 8))])
+def test_mixed_be_viscosity_three_components(oracle_mod, R, pc, dims, block):
     O = oracle_mod
-    dims = (16, 12, 24)
     v = synth.viscosity_case(*dims, seed=1)
     g = O.Grid(v["rf"], dims[1], dims[2])
     S, W = O.assemble_viscosity(g, v["rho"], v["nu"])
     ctx = R.Context(v["rf"], dims[1], dims[2], prec=R.RKL_F32MIX)
     dte = ctx.set_viscosity(dev(v["rho"]), dev(v["nu"]))
     u = dev(v["v"])
-    code, its, rel = ctx.be_pcg_solve(u, 500 * dte, pc=2, block=(4, 4, 4), rtol=1e-10, maxit=20000, ncomp=3)
+    code, its, rel = ctx.be_pcg_solve(u, 500 * dte, pc=pc, block=block, rtol=1e-10, maxit=20000, ncomp=3)
     assert code == R.RKL_OK and max(rel) <= 1e-10
     out = u.cpu().numpy().reshape((3,) + g.shape)
     Wg = W.reshape(g.shape)
