@@ -742,14 +742,32 @@ __global__ void __launch_bounds__(AB) k_bilu_apply(Dims d, IluPlan pl,
     __syncthreads();
   }
   double v2[2] = {0.0, 0.0};
+  // r.z and r.r: FP64 products per cell for the FP64 solve; for the FP32 solve the
+  // products of four successive cells of a thread are summed in FP32 before the FP64
+  // accumulation, as in the FP32 SpMV and Jacobi update
+  T prz = T(0), prr = T(0);
+  int cnt = 0;
   for (int q = tid; q < gcount * bs; q += AB) {
     const int bb = q / bs;
     const long long c = base[bb] + goff[q - bb * bs];
     const T zv = zs[bb * zst + (q - bb * bs)], rv = r[c];
     z[c] = zv;
-    v2[0] = fma((double)rv, (double)zv, v2[0]);
-    v2[1] = fma((double)rv, (double)rv, v2[1]);
+    if constexpr (std::is_same<T, float>::value) {
+      prz = fmaf(rv, zv, prz);
+      prr = fmaf(rv, rv, prr);
+      if (++cnt == 4) {
+        v2[0] += (double)prz;
+        v2[1] += (double)prr;
+        prz = prr = 0.f;
+        cnt = 0;
+      }
+    } else {
+      v2[0] = fma(rv, zv, v2[0]);
+      v2[1] = fma(rv, rv, v2[1]);
+    }
   }
+  v2[0] += (double)prz;
+  v2[1] += (double)prr;
   double tot[2];
   if (grid_sum<2, AB>(v2, partials, counter, tot) && threadIdx.x == 0) finalize_dots(st, tot[0], tot[1], init != 0);
 }
