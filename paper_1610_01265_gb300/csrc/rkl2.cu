@@ -125,7 +125,9 @@ __global__ void __launch_bounds__(BLK) k_rkl2_stage_mix(Dims d, const float *__r
 // The same stage for symmetric conduction and viscosity, marching along phi with the
 // planes of delta_{j-1} and of the coefficients brought in by bulk copies (march.cuh);
 // per cell the arithmetic of k_rkl2_stage_mix<OP>.  Yout may alias dm2 (each cell is read
-// by its own thread, a plane ahead of its write).
+// by its own thread, a plane ahead of its write).  LAST (u += delta_s in FP64) is a
+// separate instantiation, so that the other stages issue no FP64 instruction at all.
+template <bool LAST>
 struct StageEpi {
   const float *__restrict__ invW;
   const float *dm2;
@@ -155,7 +157,7 @@ struct StageEpi {
       t = fmaf(mutdt, f, t);
       y[e] = fmaf(cm0, mv[e], t);
     }
-    if (u) {
+    if constexpr (LAST) {
 #pragma unroll
       for (int e = 0; e < 4; e++) u[c + e] += (double)y[e];
     } else {
@@ -164,7 +166,7 @@ struct StageEpi {
   }
   __device__ __forceinline__ void poison(long long c) {
     const float q = __int_as_float(0x7fc00000);
-    if (u) {
+    if constexpr (LAST) {
 #pragma unroll
       for (int e = 0; e < 4; e++) u[c + e] = (double)q;
     } else {
@@ -173,7 +175,7 @@ struct StageEpi {
   }
 };
 
-template <int OP>
+template <int OP, bool LAST>
 __global__ void __launch_bounds__(MARCH_MAX_THREADS, 1) k_rkl2_stage_mix_tma(Dims d, int nchunk,
                                                                         const float *__restrict__ coef,
                                                                         const float *__restrict__ invW,
@@ -183,7 +185,7 @@ __global__ void __launch_bounds__(MARCH_MAX_THREADS, 1) k_rkl2_stage_mix_tma(Dim
                                                                         float *dout, double *u, float mu,
                                                                         float nu, float mutdt, float cm0,
                                                                         int *kerr) {
-  StageEpi e{invW, dm2, M0f, dout, u, mu, nu, mutdt, cm0};
+  StageEpi<LAST> e{invW, dm2, M0f, dout, u, mu, nu, mutdt, cm0};
   march32<OP>(d, nchunk, coef, dm1, e, kerr);
 }
 
@@ -202,13 +204,15 @@ int march_setup_stage(rkl_ctx *ctx) {
   if (rc) return rc;
   for (int op = OPK_COND; op <= OPK_VISC; op++)
     if ((size_t)optin < march_smem(ctx->d.nr, op) + 1024) ctx->march_nchunk[op] = 0;
-  rc = cuda_check(ctx, cudaFuncSetAttribute(k_rkl2_stage_mix_tma<OPK_COND>,
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize, optin - 1024),
-                  "bulk-copy stage shared memory");
-  if (rc) return rc;
-  return cuda_check(ctx, cudaFuncSetAttribute(k_rkl2_stage_mix_tma<OPK_VISC>,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize, optin - 1024),
-                    "bulk-copy stage shared memory");
+  const void *kerns[] = {(const void *)k_rkl2_stage_mix_tma<OPK_COND, false>,
+                         (const void *)k_rkl2_stage_mix_tma<OPK_COND, true>,
+                         (const void *)k_rkl2_stage_mix_tma<OPK_VISC, false>,
+                         (const void *)k_rkl2_stage_mix_tma<OPK_VISC, true>};
+  for (const void *k : kerns)
+    if ((rc = cuda_check(ctx, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - 1024),
+                         "bulk-copy stage shared memory")))
+      return rc;
+  return RKL_OK;
 }
 
 int launch_to_float(rkl_ctx *ctx, const double *a, float *b, long long n) {
@@ -236,14 +240,15 @@ int launch_rkl2_stage_mix(rkl_ctx *ctx, const float *dm1, const float *dm2, cons
     const int TH = march_th(ctx->d.nr), nchunk = ctx->march_nchunk[ctx->op];
     const unsigned grid = (unsigned)(((ctx->d.nth + TH - 1) / TH) * nchunk);
     const dim3 block(march_threads(ctx->d.nr));
+    const size_t smem = march_smem(ctx->d.nr, ctx->op);
+    auto go = [&](auto kern) {
+      kern<<<grid, block, smem, ctx->stream>>>(ctx->d, nchunk, ctx->coef32, ctx->invW32, dm1, dm2, M0f, dout, u,
+                                                (float)mu, (float)nu, (float)mutdt, (float)cm0, ctx->d_kerr);
+    };
     if (ctx->op == OPK_COND)
-      k_rkl2_stage_mix_tma<OPK_COND><<<grid, block, march_smem(ctx->d.nr, OPK_COND), ctx->stream>>>(
-          ctx->d, nchunk, ctx->coef32, ctx->invW32, dm1, dm2, M0f, dout, u, (float)mu, (float)nu, (float)mutdt,
-          (float)cm0, ctx->d_kerr);
+      u ? go(k_rkl2_stage_mix_tma<OPK_COND, true>) : go(k_rkl2_stage_mix_tma<OPK_COND, false>);
     else
-      k_rkl2_stage_mix_tma<OPK_VISC><<<grid, block, march_smem(ctx->d.nr, OPK_VISC), ctx->stream>>>(
-          ctx->d, nchunk, ctx->coef32, ctx->invW32, dm1, dm2, M0f, dout, u, (float)mu, (float)nu, (float)mutdt,
-          (float)cm0, ctx->d_kerr);
+      u ? go(k_rkl2_stage_mix_tma<OPK_VISC, true>) : go(k_rkl2_stage_mix_tma<OPK_VISC, false>);
     ctx->launches += 1;
     return cuda_check(ctx, cudaGetLastError(), "mixed rkl2 stage launch");
   }
