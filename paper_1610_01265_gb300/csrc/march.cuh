@@ -11,8 +11,9 @@
 //         viscosity slot 1 of row j0-1                               ring of MC = 4 planes
 // which is all that the stencil of plane k reads: u of planes k-1, k, k+1, the
 // coefficients of plane k, and the backward entries held by plane k-1 (conduction slots
-// 2, 5, 6, 7, 8; viscosity slot 2).  Each plane of every stream is copied once per tile, so the only traffic above
-// the algorithmic bytes is the theta halo, which the neighbouring tile reads from L2.
+// 2, 5, 6, 7, 8; viscosity slot 2).  Each plane of every stream is copied once per tile,
+// so the only traffic above the algorithmic bytes is the theta halo, which the
+// neighbouring tile reads from L2.
 // While plane k is computed, the copies of u up to plane k+3 and of the coefficients
 // up to plane k+2 are in flight.  One elected thread issues them, in batches that each
 // complete one of three mbarriers:
@@ -43,8 +44,9 @@ constexpr long long MARCH_WAIT_CYCLES = 4000000000LL;  // ~2 s at the maximum SM
 __host__ __device__ inline bool march_ok(int nr) { return nr % 4 == 0 && nr >= 4 && nr <= 256; }
 // theta rows per tile: at least 4 (halo rows cost 2 per tile) and at least 512 cells per
 // plane; a CTA has one thread per four cells of a tile plane, rounded up to whole warps,
-// so tiles of nr <= 128 take 128 threads and about 108 KB (two CTAs per SM), tiles of
-// nr = 256 take 256 threads and about 215 KB
+// so tiles of nr <= 128 take 128 threads and (conduction) about 108 KB of shared memory,
+// two CTAs per SM; tiles of nr = 256 take 256 threads and about 215 KB (viscosity needs
+// less than half of these)
 __host__ __device__ inline int march_th(int nr) { return 128 / (nr / 4) > 4 ? 128 / (nr / 4) : 4; }
 __host__ __device__ inline int march_threads(int nr) { return ((nr / 4) * march_th(nr) + 31) / 32 * 32; }
 // coefficient slots of a tile row and halo rows per plane
