@@ -78,9 +78,9 @@ enum { RKL_F64 = 0, RKL_F32MIX = 1 };
  *   keeps FP32 copies of the operator; rkl2_superstep runs the stages in FP32 on the
  *   increments Y_j - Y_0 with FP64 stage coefficients, M0 = F(Y0) in FP64 and the
  *   result Y_0 + (Y_s - Y_0) formed in FP64; be_pcg_solve is FP64 iterative refinement
- *   (FP64 residual and stopping test, FP32 PCG correction solves with FP64 dot
- *   products, FP64 update), so it meets the same rtol; iters_out then counts FP32
- *   iterations.  apply_F stays FP64.
+ *   (FP64 residual and stopping test, FP32 PCG correction solves whose dot products
+ *   are accumulated in FP64 from FP32 partials of a few cells, FP64 update), so it
+ *   meets the same rtol; iters_out then counts FP32 iterations.  apply_F stays FP64.
  * cuda_stream: a cudaStream_t (NULL = legacy default stream) on which all work of
  * this context is queued.  Allocates the geometry tables; coefficient, stage and
  * Krylov buffers are allocated on first use and kept until rkl_destroy. */
