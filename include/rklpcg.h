@@ -13,7 +13,8 @@
  * 7-point for viscosity) and W the cell heat capacity (3 k n V) or mass (rho V).
  *
  * Grid and layout.  nr x nth x nph cells; radial faces given by the caller (any
- * strictly increasing positive radii, in units of R_sun = 6.96e10 cm); theta faces
+ * strictly increasing positive radii, in units of rkl_grid.rsun_cm, by default
+ * R_sun = 6.96e10 cm); theta faces
  * j pi / nth (cell-centred, zero-area pole faces); phi faces k 2 pi / nph, periodic.
  * Zero-flux boundaries at the first and last radial face.  Every field is a
  * contiguous float64 array indexed ((k * nth) + j) * nr + i, r fastest; a field of
@@ -50,7 +51,9 @@ typedef struct rkl_ctx rkl_ctx;
 
 typedef struct {
   int nr, nth, nph;       /* cells along r, theta, phi: nr >= 1, 1 <= nth, 3 <= nph, both <= 65535 */
-  const double *r_faces;  /* HOST array of nr+1 radial faces (R_sun), copied at create */
+  const double *r_faces;  /* HOST array of nr+1 radial faces in units of rsun_cm, copied at create */
+  double rsun_cm;         /* length unit of r_faces in cm; 0 selects R_sun = 6.96e10 cm
+                             (negative or non-finite: RKL_EINVAL) */
 } rkl_grid;
 
 enum {
@@ -117,6 +120,14 @@ enum {
  * and the number of counted launches of one family. */
 int rkl_profile_enable(rkl_ctx *ctx, int on);
 int rkl_profile_read(rkl_ctx *ctx, int kernel, double *total_ms, long long *launches);
+
+/* Measured FP64 fused-multiply-add throughput of the current device in TFLOP/s (2 flop
+ * per FMA), the roof of the FP64 stencil kernels (instrumentation for the roofline; no
+ * paper counterpart).  Runs a kernel of 8 independent FMA chains per thread on 8 CTAs of
+ * 256 threads per SM, for about 50 ms, on cuda_stream (NULL = legacy default stream),
+ * three times after a warm-up, and reports the fastest; synchronises the stream.  It
+ * allocates and frees a small result buffer (2.5 MB on 152 SMs). */
+int rkl_fp64_peak(void *cuda_stream, double *tflops_out);
 
 /* Number of CUDA kernels this context has launched since rkl_create (instrumentation:
  * every launch of every entry point is counted, including PCG iterations queued after
@@ -206,14 +217,17 @@ int be_pcg_solve(rkl_ctx *ctx, double *u, int ncomp, double dt, int pc, const in
  * hence nr <= 1024, nth <= 1024 and nr*nth*nph <= 65536 cells (RKL_EINVAL beyond).
  * T [N], bhat [3N], n [N] and u [N] must be device pointers (RKL_EINVAL otherwise); u is
  * advanced in place.  kappa0 and coeff_flags are those of set_coeffs (RKL_BETA_TCUT
- * only: RKL_FLUX_FORM is RKL_EINVAL); dt, s (0: Eq. 5
- * with the dt_exp computed here) and flags those of rkl2_superstep.  dt_exp_out and
- * s_used (host, may be NULL) receive dt_exp and the number of stages.
+ * only: RKL_FLUX_FORM is RKL_EINVAL); dt and flags are those of rkl2_superstep; s > 0
+ * runs exactly s stages, s == 0 the stage count that rkl2_stage_count gives for dt over
+ * the dt_exp computed here.  dt_exp_out and s_used (host, may be NULL) receive dt_exp and
+ * the number of stages.
  * The first call on a device looks up the device address of the static array with that
  * device current (cudaGetSymbolAddress); make that first call before any stream capture.
  * All calls on a device share the array, which keeps the last call's contents: calls
- * that overlap on the GPU (several streams or host threads) race and must be serialised
- * by the caller.  The call returns once dt_exp is known (one small device-to-host read);
+ * that overlap on the GPU (several streams, or host threads driving the same device)
+ * race on it and must be serialised by the caller.  The host-side steps (the address
+ * look-up, the staging of the geometry tables) are serialised by the library, so calls
+ * from several host threads on different devices do not interfere.  The call returns once dt_exp is known (one small device-to-host read);
  * the stage kernels then run asynchronously on cuda_stream. */
 int rkl2_superstep_noalloc(const rkl_grid *g, const double *T, const double *bhat,
                            const double *n, double kappa0, int coeff_flags, double *u,

@@ -13,6 +13,7 @@
 
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "internal.cuh"
 
@@ -45,8 +46,13 @@ static __device__ __align__(256) double rkl_noalloc_scratch[kScratchDoubles];
 // Device address of rkl_noalloc_scratch per device, looked up once (host-side name of a
 // __device__ array is not a device address).
 static double *g_scratch_addr[RKL_NOALLOC_MAX_DEVICES] = {nullptr};
-// Host copy of the geometry tables of the last call (no heap use).
+// Host copy of the geometry tables of the call being staged (no heap use).
 static double g_geo_host[kGeo];
+// Guards g_scratch_addr and g_geo_host: calls from several host threads (on one device or
+// on several) serialise the address look-up and the fill + upload of the geometry tables.
+// An upload from pageable memory returns once the source has been staged, so the buffer
+// is free again when the lock is released.
+static std::mutex g_host_mu;
 
 bool device_resident(const void *p) {
   cudaPointerAttributes at;
@@ -64,7 +70,7 @@ double stage_b(int j) { return j <= 2 ? 1.0 / 3.0 : ((double)j * j + j - 2.0) / 
 void fill_geometry(const rkl_grid *g) {
   const int nr = g->nr, nth = g->nth, nph = g->nph;
   const double *rf = g->r_faces;
-  const double RS = RKL_RSUN_CM;
+  const double RS = g->rsun_cm > 0.0 ? g->rsun_cm : RKL_RSUN_CM;
   const double dth = RKL_PI / nth;
   (void)nph;
   double *rc = g_geo_host, *hr = rc + RKL_NOALLOC_MAX_NR, *dr = hr + RKL_NOALLOC_MAX_NR;
@@ -99,6 +105,7 @@ extern "C" int rkl2_superstep_noalloc(const rkl_grid *g, const double *T, const 
                                       double *dt_exp_out, int *s_used) {
   // ---- arguments (nothing is touched on the device before they pass) ----
   if (!g || !g->r_faces || g->nr < 1 || g->nth < 1 || g->nph < 3) return RKL_EINVAL;
+  if (!(g->rsun_cm == 0.0 || (std::isfinite(g->rsun_cm) && g->rsun_cm > 0.0))) return RKL_EINVAL;
   if (g->nr > RKL_NOALLOC_MAX_NR || g->nth > RKL_NOALLOC_MAX_NTH ||
       (long long)g->nr * g->nth * g->nph > RKL_NOALLOC_MAX_CELLS)
     return RKL_EINVAL;  // larger than the static scratch
@@ -117,6 +124,7 @@ extern "C" int rkl2_superstep_noalloc(const rkl_grid *g, const double *T, const 
   // ---- per-device set-up: the device address of the static scratch ----
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= RKL_NOALLOC_MAX_DEVICES) return RKL_ECUDA;
+  std::unique_lock<std::mutex> host_lock(g_host_mu);
   if (!g_scratch_addr[dev]) {
     double *p = nullptr;
     if (cudaGetSymbolAddress((void **)&p, rkl_noalloc_scratch) != cudaSuccess || !p) {
@@ -156,6 +164,7 @@ extern "C" int rkl2_superstep_noalloc(const rkl_grid *g, const double *T, const 
   fill_geometry(g);
   if (cudaMemcpyAsync(sc, g_geo_host, kGeo * sizeof(double), cudaMemcpyHostToDevice, stream) != cudaSuccess)
     return RKL_ECUDA;
+  host_lock.unlock();
   // the Gershgorin maximum and the error flag must start at zero on every call
   if (cudaMemsetAsync(lam, 0, 2 * sizeof(double), stream) != cudaSuccess) return RKL_ECUDA;
   if (launch_setup_conduction_raw(d, geo, stream, T, bhat, n, kappa0, coeff_flags, kappa, FS, W, invW,
