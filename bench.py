@@ -10,10 +10,19 @@ One step = one pass over every step of the path, through the C ABI:
 Metric: cell-updates/s = cells x (RKL2 stages + PCG iterations, per component) / time.
 
 Timing: W untimed warm-up steps, then K steps between barriers and device syncs, CUDA
-events on the library's stream, max over ranks.  The working set of every stage pass
-(~1.2 GB) is far larger than the 129 MB L2, so no flush is needed between steps.
-Several GPUs (torchrun) run independent replicas (one grid per GPU, no exchange).
-`--impl reference` times the FP64 CPU oracle instead (bounded sample, host cores).
+events on the library's stream, max over ranks, on the library's default path (the
+RKL2 super-steps and the PCG loops run as CUDA graphs).  The per-kernel times of the
+roofline come from one more step run right after, with the library's event profiler on
+(every launch bracketed by events, graphs off), so that the timed steps carry no
+instrumentation.  The working set of every stage pass (~1.2 GB) is far larger than the
+129 MB L2, so no flush is needed between steps.  Several GPUs (torchrun) run independent
+replicas (one grid per GPU, no exchange).  `--impl reference` times the FP64 CPU oracle
+instead (bounded sample, host cores).
+
+The line's `detail` also times, once, the other configurations of the comparison:
+32 x 32 x 64 (RKL2 and BE + PCG-Jacobi, FP64, next to the oracle's full run of the same on
+the host cores), 256 x 384 x 768 (mixed precision against FP64) and 192 x 288 x 576
+(viscosity, FP64 against FP32 mixed precision, RKL2 against BE + PCG-Jacobi).
 """
 from __future__ import annotations
 
@@ -38,7 +47,7 @@ VISC_RATIO = 500.0
 RTOL = 1e-10
 MAXIT = 20000
 BLOCK = (8, 8, 8)
-BETA_TCUT = True  # conduction coefficient evaluated at max(T, 5e5 K), as in the paper's runs (Sec. 4.1)
+BETA_TCUT = True  # kappa0 T^{5/2} times the printed factor (T / 5e5 K)^{5/2} below 5e5 K (Sec. 4.1 beta_Tcut)
 FP64_PEAK_TFLOPS = 1.25  # nominal FP64 rate of the GB300 (2 DFMA/clk/SM x 152 SMs x 2.07 GHz)
 # Algorithmic cost per cell of one launch of each kernel family (one field component):
 # (flop, bytes, binding unit, ncu summary, sources the summary was taken on).
@@ -53,11 +62,18 @@ FP64_PEAK_TFLOPS = 1.25  # nominal FP64 rate of the GB300 (2 DFMA/clk/SM x 152 S
 KERNEL_COST = {
     ("conduction", "rkl2_stage"): (48.0, 128.0, "alu", "rkl2_stage_128x192x384.md",
                                    ("rkl2.cu:k_rkl2_stage", "stencil.cuh")),
-    ("viscosity", "rkl2_stage"): (24.0, 80.0, "alu", None, ()),
+    ("viscosity", "rkl2_stage"): (24.0, 80.0, "alu", "rkl2_stage_visc_128x192x384.md",
+                                  ("rkl2.cu:k_rkl2_stage", "stencil.cuh")),
     ("conduction", "spmv"): (40.0, 96.0, "alu", "spmv_128x192x384.md", ("pcg.cu:k_spmv_a", "stencil.cuh")),
-    ("viscosity", "spmv"): (16.0, 48.0, "alu", None, ()),
+    ("viscosity", "spmv"): (16.0, 48.0, "alu", "spmv_visc_128x192x384.md", ("pcg.cu:k_spmv_a", "stencil.cuh")),
     ("conduction", "bilu_apply"): (41.0, 168.0, "alu", "bilu_apply_128x192x384.md", ("pcg.cu:k_bilu_apply",)),
-    ("viscosity", "bilu_apply"): (17.0, 72.0, "alu", None, ()),
+    ("viscosity", "bilu_apply"): (17.0, 72.0, "alu", "bilu_apply_visc_128x192x384.md", ("pcg.cu:k_bilu_apply",)),
+}
+# part of the demangled ncu kernel name of each family (for --summarize-ncu)
+FAMILY_KERNEL = {
+    ("conduction", "rkl2_stage"): "k_rkl2_stage<0>", ("viscosity", "rkl2_stage"): "k_rkl2_stage<1>",
+    ("conduction", "spmv"): "k_spmv_a<0>", ("viscosity", "spmv"): "k_spmv_a<1>",
+    ("conduction", "bilu_apply"): "k_bilu_apply<0, double>", ("viscosity", "bilu_apply"): "k_bilu_apply<1, double>",
 }
 WORKLOAD = "coronal FP64 conduction+viscosity, 128x192x384 spherical grid"
 
@@ -77,8 +93,18 @@ def parse_args():
     p.add_argument("--warmstart", action="store_true",
                    help="run the learned-initial-guess study (200 BE steps with heating) instead of the step")
     p.add_argument("--profile", choices=("stage", "apply", "pcg-jacobi", "pcg-bilu0", "setup", "stage-mix",
-                                         "pcg-jacobi-mix", "pcg-bilu0-mix", "ws-forward", "ws-train"),
+                                         "pcg-jacobi-mix", "pcg-bilu0-mix", "ws-forward", "ws-train",
+                                         "visc-stage", "visc-pcg-jacobi", "visc-pcg-bilu0"),
                    help="run only a minimal case of one kernel family for an ncu capture (no timing)")
+    p.add_argument("--plain-launches", action="store_true",
+                   help="run every step with the library's event profiler on (plain launches, no graphs), so "
+                        "that an ncu launch list sees every kernel; not a bench number")
+    p.add_argument("--no-configs", action="store_true",
+                   help="skip the 32x32x64, 256x384x768 and 192x288x576 lines of detail")
+    p.add_argument("--summarize-ncu", nargs=3, metavar=("REPORT", "FAMILY", "OUT"),
+                   help="write a profile summary (metrics, traffic, source hash, capture date) of the kernel of "
+                        "FAMILY (e.g. conduction/spmv) from an ncu report, then exit")
+    p.add_argument("--summary-command", default="", help="command line recorded in the --summarize-ncu summary")
     return p.parse_args()
 
 
@@ -101,6 +127,7 @@ def base_config():
         "beta_tcut": BETA_TCUT,
         "viscosity_dt_over_dt_exp": VISC_RATIO,
         "l2": "no flush: every stage pass streams ~1.2 GB, far above the 129 MB L2",
+        "graphs": "library default: RKL2 super-steps and PCG loops replayed as CUDA graphs in the timed steps",
     }
 
 
@@ -133,6 +160,83 @@ def cpu_sample_text():
     return ("conduction on the full 128x192x384 grid: one RKL2 super-step of 4 stages, "
             "4 PCG-Jacobi and 4 PCG-block-ILU0(8^3) iterations (ILU factorisation "
             "included), operator assembly excluded; cell-updates = cells x 12")
+
+
+C1_GRID = (32, 32, 64)
+C1_RATIO = 100.0
+
+
+def cpu_model():
+    """Host CPU model and core count (lscpu, else /proc/cpuinfo)."""
+    name = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                name = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not name:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu part")):
+                    name = line.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    import platform
+
+    return {"model": name or platform.processor() or platform.machine(), "machine": platform.machine(),
+            "logical_cpus": os.cpu_count()}
+
+
+def cpu_c1_full(seed: int, threads: int | None = None):
+    """The oracle's full run of the 32 x 32 x 64 configuration on the host cores: conduction
+    with beta_Tcut, one RKL2 super-step at 100 dt_exp (s = 20) and one BE step by PCG-Jacobi
+    to rtol 1e-10 at the same dt; operator assembly and Gershgorin timed separately."""
+    import oracle as O
+
+    from paper_1610_01265_gb300 import synth
+
+    nr, nth, nph = C1_GRID
+    c = synth.conduction_case(nr, nth, nph, seed)
+    g = O.Grid(c["rf"], nth, nph)
+    prev = O.num_threads()
+    if threads:
+        O.set_num_threads(threads)
+    try:
+        used = O.num_threads()
+        t0 = time.perf_counter()
+        S, W = O.assemble_conduction(g, c["T"], c["bhat"], c["n"], beta_tcut=BETA_TCUT)
+        dte, _ = O.gershgorin_dt(g, S, W)
+        t1 = time.perf_counter()
+        s = O.rkl2_stages(C1_RATIO)
+        O.rkl2_superstep(g, S, W, c["T"], C1_RATIO * dte, s)
+        t2 = time.perf_counter()
+        _, its, rel, st = O.be_pcg(g, S, W, c["T"], C1_RATIO * dte, pc=O.PC_JACOBI, rtol=RTOL, maxit=MAXIT)
+        t3 = time.perf_counter()
+    finally:
+        O.set_num_threads(prev)
+    units = g.N * (s + its)
+    return {"threads": used, "setup_ms": 1e3 * (t1 - t0), "rkl2_ms": 1e3 * (t2 - t1), "s": s,
+            "be_jacobi_ms": 1e3 * (t3 - t2), "be_jacobi_iters": its, "be_converged": st == 0,
+            "cell_updates_per_s": units / (t3 - t1)}
+
+
+def cpu_baseline_leg(seed: int):
+    """cpu_baseline of the bench line: the bounded sample of the timed workload on all host
+    cores (value), plus a single-thread rate and the oracle's full 32 x 32 x 64 run."""
+    run, units, cores = cpu_sample(seed)
+    t = run()
+    out = {"value": units / t, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
+           "sample": cpu_sample_text(), "seconds": t, "host": cpu_model()}
+    one = cpu_c1_full(seed, threads=1)
+    out["single_thread"] = {"value": one["cell_updates_per_s"], "unit": "cell-updates/s", "cores": 1,
+                            "sample": "the oracle's full 32x32x64 run (RKL2 s=20 + BE-Jacobi to 1e-10 at "
+                                      "100 dt_exp), one thread", "detail": one}
+    out["c1_full_all_cores"] = cpu_c1_full(seed)
+    return out
 
 
 def run_reference(args):
@@ -547,6 +651,121 @@ def seeds_report(wl, torch, seeds=(2, 3)):
     return out
 
 
+def _timed(torch, fn, reps=1):
+    """(result of the last call, median ms) of fn() on the current stream, CUDA events."""
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms, r = [], None
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        e0.record()
+        r = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return r, statistics.median(ms)
+
+
+def c1_report(R, torch, seed: int):
+    """32 x 32 x 64 (the configuration the oracle runs in full): conduction with beta_Tcut,
+    RKL2 at 100 dt_exp and BE + PCG-Jacobi to rtol 1e-10 at the same dt, FP64, ms per large
+    step (median of 5 after a warm-up, default path), with the difference from the oracle."""
+    import oracle as O
+
+    from paper_1610_01265_gb300 import synth
+
+    nr, nth, nph = C1_GRID
+    N = nr * nth * nph
+    c = synth.conduction_case(nr, nth, nph, seed)
+    dev = lambda a: torch.from_numpy(np.array(a, dtype=np.float64).ravel()).cuda()  # noqa: E731
+    T, b, n = dev(c["T"]), dev(c["bhat"]), dev(c["n"])
+    out = {"grid_nr_nth_nph": list(C1_GRID), "cells": N, "dt_over_dt_exp": C1_RATIO, "rtol": RTOL,
+           "beta_tcut": BETA_TCUT}
+    with R.Context(c["rf"], nth, nph) as ctx:
+        dte, out["set_coeffs_ms"] = _timed(torch, lambda: ctx.set_conduction(T, b, n, beta_tcut=BETA_TCUT), 5)
+        u = torch.empty_like(T)
+
+        def rk():
+            u.copy_(T)
+            return ctx.rkl2_superstep(u, C1_RATIO * dte, dte)
+
+        rk()
+        s, ms = _timed(torch, rk, 5)
+        g = O.Grid(c["rf"], nth, nph)
+        S, W = O.assemble_conduction(g, c["T"], c["bhat"], c["n"], beta_tcut=BETA_TCUT)
+        ref = O.rkl2_superstep(g, S, W, c["T"], C1_RATIO * dte, s)
+        err = float(np.linalg.norm(u.cpu().numpy() - ref.ravel()) / np.linalg.norm(ref))
+        out["rkl2"] = {"s": s, "ms": ms, "cell_updates_per_s": N * s / ms * 1e3, "rel_l2_vs_oracle": err}
+
+        def be():
+            u.copy_(T)
+            return ctx.be_pcg_solve(u, C1_RATIO * dte, pc=R.RKL_PC_JACOBI, rtol=RTOL, maxit=MAXIT)
+
+        be()
+        (code, its, rel), ms = _timed(torch, be, 5)
+        x_o, it_o, _, _ = O.be_pcg(g, S, W, c["T"], C1_RATIO * dte, pc=O.PC_JACOBI, rtol=RTOL, maxit=MAXIT)
+        out["be_jacobi"] = {"iters": its[0], "oracle_iters": it_o, "ms": ms, "relres": rel[0],
+                            "converged": code == R.RKL_OK, "cell_updates_per_s": N * its[0] / ms * 1e3,
+                            "rel_l2_vs_oracle": float(np.linalg.norm(u.cpu().numpy() - x_o.ravel())
+                                                      / np.linalg.norm(x_o))}
+    return out
+
+
+C4_GRID = (192, 288, 576)
+
+
+def c4_report(R, torch, seed: int):
+    """192 x 288 x 576 viscosity on the three Cartesian components at 500 dt_exp: FP64 against
+    FP32 mixed precision, RKL2 (s = 45) against BE + PCG-Jacobi to rtol 1e-10; ms per large
+    step, and the difference of each result from the FP64 one relative to the step's
+    change."""
+    from paper_1610_01265_gb300 import synth
+
+    nr, nth, nph = C4_GRID
+    N = nr * nth * nph
+    v = synth.viscosity_case(nr, nth, nph, seed)
+    dev = lambda a: torch.from_numpy(np.array(a, dtype=np.float64).ravel()).cuda()  # noqa: E731
+    rho, nu, V = dev(v["rho"]), dev(v["nu"]), dev(v["v"])
+    rf = v["rf"]
+    del v
+    out = {"grid_nr_nth_nph": list(C4_GRID), "cells": N, "components": 3, "dt_over_dt_exp": VISC_RATIO,
+           "rtol": RTOL}
+    res = {}
+    u = torch.empty_like(V)
+    for prec, pname in ((R.RKL_F64, "fp64"), (R.RKL_F32MIX, "fp32_mixed")):
+        with R.Context(rf, nth, nph, prec=prec) as ctx:
+            dte, set_ms = _timed(torch, lambda: ctx.set_viscosity(rho, nu))
+            dt = VISC_RATIO * dte
+
+            def rk():
+                u.copy_(V)
+                return ctx.rkl2_superstep(u, dt, dte, ncomp=3)
+
+            rk()
+            s, ms_rk = _timed(torch, rk, 3)
+            y_rk = u.clone()
+
+            def be():
+                u.copy_(V)
+                return ctx.be_pcg_solve(u, dt, pc=R.RKL_PC_JACOBI, rtol=RTOL, maxit=MAXIT, ncomp=3)
+
+            be()
+            (code, its, rel), ms_be = _timed(torch, be, 3)
+            res[pname] = {"rkl2": y_rk, "be": u.clone()}
+            out[pname] = {"set_coeffs_ms": set_ms, "dt_exp_s": dte,
+                          "rkl2": {"s": s, "ms": ms_rk, "cell_updates_per_s": 3 * N * s / ms_rk * 1e3},
+                          "be_jacobi": {"iters": its, "ms": ms_be, "relres": max(rel), "converged": code == R.RKL_OK,
+                                        "cell_updates_per_s": N * sum(its) / ms_be * 1e3}}
+    for path in ("rkl2", "be"):
+        ref = res["fp64"][path]
+        chg = torch.linalg.vector_norm(ref - V).item()
+        key = path if path == "rkl2" else "be_jacobi"
+        out["fp32_mixed"][key]["err_rel_change_vs_fp64"] = torch.linalg.vector_norm(
+            res["fp32_mixed"][path] - ref).item() / chg
+    out["rkl2_vs_be_fp64_rel_change"] = (torch.linalg.vector_norm(res["fp64"]["rkl2"] - res["fp64"]["be"]).item()
+                                         / torch.linalg.vector_norm(res["fp64"]["be"] - V).item())
+    return out
+
+
 def aggregate(ms: float, units: float, dist=None, device=None):
     """Whole-job figures of independent replicas: the slowest rank's time and the sum of
     the cell-updates of all ranks (value = units / time).  dist None = one process."""
@@ -610,6 +829,20 @@ def profile_case(args):
         return 0
     mixed = args.profile.endswith("-mix")
     ctx = R.Context(c["rf"], nth, nph, prec=R.RKL_F32MIX if mixed else R.RKL_F64)
+    if args.profile.startswith("visc-"):
+        v = synth.viscosity_case(nr, nth, nph, args.seed)
+        dte = ctx.set_viscosity(dev(v["rho"]), dev(v["nu"]))
+        V = dev(v["v"])
+        ctx.profile_enable(True)  # plain launches (see below)
+        if args.profile == "visc-stage":
+            ctx.rkl2_superstep(V, 10 * dte, dte, s=4, ncomp=3)
+        else:
+            pc = R.RKL_PC_JACOBI if args.profile == "visc-pcg-jacobi" else R.RKL_PC_BILU0
+            ctx.be_pcg_solve(V, 100 * dte, pc=pc, block=BLOCK, rtol=0.0, maxit=3, ncomp=3)
+        torch.cuda.synchronize()
+        ctx.close()
+        print(f"profile case {args.profile} done")
+        return 0
     dte = ctx.set_conduction(T, b, n, beta_tcut=BETA_TCUT)
     # the library's own profiler runs the solver loops as plain launches: ncu cannot
     # profile the kernel nodes of a graph that holds a conditional (while) node
@@ -630,6 +863,91 @@ def profile_case(args):
     torch.cuda.synchronize()
     ctx.close()
     print(f"profile case {args.profile} done")
+    return 0
+
+
+# ------------------------------------------------------------------ ncu summaries
+NCU_METRICS = (
+    ("gpu__time_duration.sum", "gpu__time_duration.sum"),
+    ("sm__cycles_elapsed.avg.per_second", "sm__cycles_elapsed.avg.per_second"),
+    ("dram__bytes_read.sum", "dram__bytes_read.sum"),
+    ("dram__bytes_write.sum", "dram__bytes_write.sum"),
+    ("gpu__dram_throughput.avg.pct_of_peak_sustained_elapsed", "gpu__dram_throughput (pct of peak, elapsed)"),
+    ("sm__pipe_fp64_cycles_active.avg.pct_of_peak_sustained_elapsed",
+     "sm__pipe_fp64_cycles_active (pct of peak, elapsed)"),
+    ("sm__inst_executed_pipe_fp64.avg.pct_of_peak_sustained_active", "FP64 pipe instructions (pct of peak, active)"),
+    ("sm__pipe_tensor_cycles_active.avg.pct_of_peak_sustained_elapsed",
+     "sm__pipe_tensor_cycles_active (pct of peak, elapsed)"),
+    ("sm__warps_active.avg.pct_of_peak_sustained_active", "sm__warps_active (pct of peak, active)"),
+    ("lts__t_sector_hit_rate.pct", "L2 hit rate (pct)"),
+    ("l1tex__data_bank_conflicts_pipe_lsu_mem_shared.sum", "shared-memory bank conflicts"),
+    ("launch__registers_per_thread", "launch__registers_per_thread"),
+    ("launch__grid_size", "launch__grid_size"),
+    ("launch__block_size", "launch__block_size"),
+)
+BYTE_UNITS = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "Tbyte": 1e12}
+
+
+def summarize_ncu(report: str, family: str, out: str, command: str) -> int:
+    """Profile summary of the first launch of FAMILY's kernel in an ncu report: the metrics
+    above, the per-launch DRAM traffic and the hash of the kernel's current source (the
+    bench takes roofline.traffic from it only while that hash matches), capture date."""
+    import csv
+    import io
+
+    key = tuple(family.split("/"))
+    pat = FAMILY_KERNEL[key]
+    txt = subprocess.run(["ncu", "-i", report, "--page", "raw", "--csv"], capture_output=True, text=True,
+                         check=True).stdout
+    rows = list(csv.reader(io.StringIO(txt)))
+    head, units = rows[0], rows[1]
+    col = {h: q for q, h in enumerate(head)}
+    sel = [r for r in rows[2:] if pat in r[col["Kernel Name"]]]
+    if not sel:
+        raise SystemExit(f"no launch of {pat} in {report}")
+    r = sel[0]
+    lines = []
+    vals = {}
+    for metric, label in NCU_METRICS:
+        if metric in col:
+            q = col[metric]
+            lines.append(f"| {label} | {r[q]} {units[q]} |")
+            vals[metric] = (r[q], units[q])
+    stalls = []
+    for h, q in col.items():
+        if h.startswith("smsp__average_warps_issue_stalled_") and h.endswith("_per_issue_active.ratio"):
+            try:
+                stalls.append((float(r[q].replace(",", "")), h[len("smsp__average_warps_issue_stalled_"):-len(
+                    "_per_issue_active.ratio")]))
+            except ValueError:
+                pass
+    stalls.sort(reverse=True)
+    if stalls:
+        lines.append("| top stalls (cycles per issue) | " + ", ".join(f"{n} {v:.2f}" for v, n in stalls[:4]) + " |")
+
+    def nbytes(m):
+        v, u = vals[m]
+        return float(v.replace(",", "")) * BYTE_UNITS.get(u, 1.0)
+
+    traffic = nbytes("dram__bytes_read.sum") + nbytes("dram__bytes_write.sum")
+    flop, alg_bytes, _, _, sources = KERNEL_COST[key]
+    cells = GRID[0] * GRID[1] * GRID[2]
+    with open(out, "w") as f:
+        f.write(f"# {r[col['Kernel Name']].split('(')[0]} ({family}) — one launch, "
+                f"{GRID[0]} x {GRID[1]} x {GRID[2]} cells\n\n")
+        f.write("Command (on one GB300; the same command first exited 0 without ncu):\n\n")
+        for cl in command.split(" ;; "):
+            f.write(f"    {cl}\n")
+        f.write(f"    python bench.py --summarize-ncu {report} {family} {out}\n\n")
+        f.write(f"Kernel: `{r[col['Kernel Name']]}`\n\n| metric | value |\n|---|---|\n")
+        f.write("\n".join(lines) + "\n\n")
+        f.write(f"Algorithmic traffic: {alg_bytes:.0f} B/cell x {cells} cells = {alg_bytes * cells / 1e9:.4f} GB; "
+                f"DRAM {traffic / 1e9:.4f} GB ({traffic / (alg_bytes * cells):.3f} of algorithmic); "
+                f"{flop:.0f} flop/cell.\n\n")
+        f.write(f"captured: {time.strftime('%Y-%m-%d', time.gmtime(os.path.getmtime(report)))}\n")
+        f.write(f"traffic_bytes_per_launch: {traffic:.0f}\n")
+        f.write(f"kernel_source_sha256_16: {kernel_source_hash(sources)}\n")
+    print(out)
     return 0
 
 
@@ -885,8 +1203,50 @@ def warmstart_study(seed=1, dims=GRID, n_steps=WS_STEPS, n_train=WS_TRAIN, ratio
     return out
 
 
+def roofline_of(prof, N, ms_step, fp64_peak, fp64_peak_note, hbm_peak):
+    """Roofline of the dominant kernel family (largest total time in the profiled step) and
+    the per-kernel table."""
+    per_kernel = {}
+    for opn, table in prof.items():
+        for kname, (tms, nl) in table.items():
+            if nl:
+                per_kernel[f"{opn}/{kname}"] = {"ms": tms, "launches": nl, "ms_per_launch": tms / nl}
+    cands = [(v["ms"], key) for key, v in per_kernel.items() if tuple(key.split("/")) in KERNEL_COST]
+    _, dom = max(cands)
+    opn, kname = dom.split("/")
+    flop, nbytes, bound, summary, sources = KERNEL_COST[(opn, kname)]
+    t_launch = per_kernel[dom]["ms_per_launch"] * 1e-3
+    achieved_tf = flop * N / t_launch / 1e12
+    total = sum(v["ms"] for v in per_kernel.values())
+    roof = {
+        "kernel": f"{kname} ({opn}, FP64)",
+        "bound": bound,
+        "achieved": achieved_tf,
+        "peak": fp64_peak,
+        "unit": "TFLOP/s",
+        "frac": achieved_tf / fp64_peak,
+        "traffic": profiled_traffic(summary, sources),
+        "traffic_source": f"profiles/{summary}" if summary else None,
+        "launch_ms": t_launch * 1e3,
+        "launches": per_kernel[dom]["launches"],
+        "share_of_step": per_kernel[dom]["ms"] / ms_step,
+        "share_of_kernel_time": per_kernel[dom]["ms"] / total,
+        "flop_per_cell": flop,
+        "bytes_per_cell": nbytes,
+        "hbm_achieved_gbs": nbytes * N / t_launch / 1e9,
+        "hbm_peak_gbs": hbm_peak,
+        "hbm_frac": nbytes * N / t_launch / 1e9 / hbm_peak,
+        "peak_note": fp64_peak_note,
+    }
+    for v in per_kernel.values():
+        v["share"] = v["ms"] / total
+    return roof, per_kernel
+
+
 def main():
     args = parse_args()
+    if args.summarize_ncu:
+        return summarize_ncu(*args.summarize_ncu, args.summary_command)
     if args.impl == "reference":
         return run_reference(args)
     if args.profile:
@@ -936,19 +1296,17 @@ def main():
     # CPU oracle baseline first (rank 0, one GPU only), before any device work
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        run, units, cores = cpu_sample(args.seed)
-        t = run()
-        cpu = {"value": units / t, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
-               "sample": cpu_sample_text(), "seconds": t}
+        cpu = cpu_baseline_leg(args.seed)
 
     wl = Workload(R, torch, args.seed + rank)
+    if args.plain_launches:
+        wl.ctx_c.profile_enable(True)
+        wl.ctx_v.profile_enable(True)
     for _ in range(max(args.warmup, 3)):
         wl.step()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    wl.ctx_c.profile_enable(True)
-    wl.ctx_v.profile_enable(True)
     launches0 = wl.launches()
     t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
@@ -966,56 +1324,48 @@ def main():
     if world > 1:
         dist.barrier()
     launches = wl.launches() - launches0
-    prof = {"conduction": wl.ctx_c.profile(), "viscosity": wl.ctx_v.profile()}
-    wl.ctx_c.profile_enable(False)
-    wl.ctx_v.profile_enable(False)
     ms = t_start.elapsed_time(t_end)
     ms, units_all = aggregate(ms, float(units), dist if world > 1 else None, "cuda")
     value = units_all / (ms * 1e-3)
 
-    # roofline of the dominant kernel: the kernel family with the largest total time in
-    # the timed region (library event timing on its stream, launches that did work only)
+    # per-kernel times: one more step with the library's event profiler on (plain launches)
+    wl.ctx_c.profile_enable(True)
+    wl.ctx_v.profile_enable(True)
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record()
+    units_p, _ = wl.step()
+    p1.record()
+    torch.cuda.synchronize()
+    ms_prof = p0.elapsed_time(p1)
+    prof = {"conduction": wl.ctx_c.profile(), "viscosity": wl.ctx_v.profile()}
+    if not args.plain_launches:
+        wl.ctx_c.profile_enable(False)
+        wl.ctx_v.profile_enable(False)
+
+    # FP64 roof: the device's measured FMA throughput
     peaks = measured_peaks()
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    per_kernel = {}
-    for opn, table in prof.items():
-        for kname, (tms, nl) in table.items():
-            if nl:
-                per_kernel[f"{opn}/{kname}"] = {"ms": tms, "launches": nl, "ms_per_launch": tms / nl}
-    cands = [(v["ms"], key) for key, v in per_kernel.items() if tuple(key.split("/")) in KERNEL_COST]
-    _, dom = max(cands)
-    opn, kname = dom.split("/")
-    flop, nbytes, bound, summary, sources = KERNEL_COST[(opn, kname)]
-    t_launch = per_kernel[dom]["ms_per_launch"] * 1e-3
-    achieved_tf = flop * wl.N / t_launch / 1e12
-    roofline = {
-        "kernel": f"{kname} ({opn}, FP64)",
-        "bound": bound,
-        "achieved": achieved_tf,
-        "peak": FP64_PEAK_TFLOPS,
-        "unit": "TFLOP/s",
-        "frac": achieved_tf / FP64_PEAK_TFLOPS,
-        "traffic": profiled_traffic(summary, sources),
-        "launch_ms": t_launch * 1e3,
-        "launches": per_kernel[dom]["launches"],
-        "share_of_step": per_kernel[dom]["ms"] / ms,
-        "flop_per_cell": flop,
-        "bytes_per_cell": nbytes,
-        "hbm_achieved_gbs": nbytes * wl.N / t_launch / 1e9,
-        "hbm_peak_gbs": hbm_peak,
-        "hbm_frac": nbytes * wl.N / t_launch / 1e9 / hbm_peak,
-        "peak_note": "FP64 peak = recipe nominal 1.25 TFLOP/s; HBM peak = measured copy (MEASURED_PEAKS.json)",
-    }
+    try:
+        fp64_peak = R.fp64_peak()
+        fp64_note = ("FP64 peak measured in this run (rkl_fp64_peak: 8 independent FMA chains per thread, 8 CTAs "
+                     "of 256 threads per SM, best of 3); HBM peak = measured copy (MEASURED_PEAKS.json)")
+    except R.RklError:
+        fp64_peak = FP64_PEAK_TFLOPS
+        fp64_note = "FP64 peak = nominal 1.25 TFLOP/s (measurement failed); HBM peak = measured copy"
+    roofline, per_kernel = roofline_of(prof, wl.N, ms_prof, fp64_peak, fp64_note, hbm_peak)
+    roofline["profiled_step_ms"] = ms_prof
+    roofline["timed_step_ms"] = ms / args.steps
     # the fused RKL2 stage kernel, whatever its share
     st = per_kernel.get("conduction/rkl2_stage")
     stage_roof = None
     if st:
         t_st = st["ms_per_launch"] * 1e-3
         stage_roof = {"launch_ms": t_st * 1e3, "tflops": 48.0 * wl.N / t_st / 1e12,
-                      "frac_fp64": 48.0 * wl.N / t_st / 1e12 / FP64_PEAK_TFLOPS,
+                      "frac_fp64": 48.0 * wl.N / t_st / 1e12 / fp64_peak,
                       "hbm_frac": 128.0 * wl.N / t_st / 1e9 / hbm_peak}
 
-    detail = {"last_step": info, "kernels": per_kernel, "rkl2_stage_kernel": stage_roof}
+    detail = {"last_step": info, "kernels": per_kernel, "rkl2_stage_kernel": stage_roof,
+              "fp64_peak_tflops_measured": fp64_peak, "profiled_step_units": units_p}
     if rank == 0:
         detail["paths"] = path_timings(wl, torch)
         if not args.no_accuracy:
@@ -1024,6 +1374,15 @@ def main():
             detail["sec6_variants"] = variants_report(wl, torch)
             detail["flux_form"] = flux_report(wl, torch)
             detail["other_seeds"] = seeds_report(wl, torch)
+        if not args.no_configs:
+            detail["c1_32x32x64"] = c1_report(R, torch, args.seed)
+            if cpu:
+                detail["c1_32x32x64"]["oracle_host_all_cores"] = cpu["c1_full_all_cores"]
+                detail["c1_32x32x64"]["oracle_host_one_thread"] = cpu["single_thread"]["detail"]
+            detail["c3_mixed_256x384x768"] = mixed_large_report(args.seed, ratios=(1000.0,))
+            torch.cuda.empty_cache()
+            detail["c4_viscosity_192x288x576"] = c4_report(R, torch, args.seed)
+            torch.cuda.empty_cache()
 
     e2e = None
     if not args.no_e2e:
@@ -1065,6 +1424,8 @@ def main():
             "clocks": clk.summary(),
             "detail": detail,
         }
+        if args.plain_launches:
+            line["note"] = "--plain-launches: every step ran with the event profiler on (not a bench number)"
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()

@@ -72,6 +72,7 @@ def _load():
             lib.or_be_pcg.argtypes = [I, I, I, P, P, P, P, D, I, P, I, D, I, P, I, P, P]
             lib.or_offsets.argtypes = [P]
             lib.or_num_threads.restype = I
+            lib.or_set_num_threads.argtypes = [I]
             _lib = lib
     return _lib
 
@@ -113,6 +114,11 @@ def offsets() -> np.ndarray:
 
 def num_threads() -> int:
     return _load().or_num_threads()
+
+
+def set_num_threads(n: int) -> None:
+    """Host threads of the parallel loops (timing only)."""
+    _load().or_set_num_threads(int(n))
 
 
 def assemble_conduction(g: Grid, T, bhat, n, kappa0: float = 9e-7, beta_tcut: bool = False,

@@ -82,6 +82,16 @@ int or_num_threads(void) {
 #endif
 }
 
+/* Number of host threads the parallel loops use (timing only; the arithmetic of every
+ * loop is the same whatever the count). */
+void or_set_num_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+
 static long cidx(const grid *g, int i, int j, int k) {
   return ((long)k * g->nth + j) * g->nr + i;
 }

@@ -63,7 +63,7 @@ bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
 int build_geometry(rkl_ctx *ctx) {
   const int nr = ctx->d.nr, nth = ctx->d.nth, nph = ctx->d.nph;
   const double *rf = ctx->rf.data();
-  const double RS = RKL_RSUN_CM;
+  const double RS = ctx->rsun_cm;
   const double dth = RKL_PI / nth, dph = 2.0 * RKL_PI / nph;
   std::vector<double> rc(nr), hr(nr), dr(nr), ar(nr), a2(nr), v3(nr), dcos(nth), stf(nth), stc(nth);
   for (int i = 0; i < nr; i++) rc[i] = 0.5 * (rf[i] + rf[i + 1]);
@@ -210,6 +210,7 @@ int rkl_create(rkl_ctx **out, const rkl_grid *g, int prec, void *stream) {
   if (g->nr < 1 || g->nth < 1 || g->nph < 3) return RKL_EINVAL;
   if (g->nth > 65535 || g->nph > 65535) return RKL_EINVAL;  // 3-D launches put (j, k) on the grid
   if ((long long)g->nr * g->nth * g->nph > (1LL << 40)) return RKL_EINVAL;
+  if (!(g->rsun_cm == 0.0 || finite_pos(g->rsun_cm))) return RKL_EINVAL;
   for (int i = 0; i <= g->nr; i++) {
     if (!finite_pos(g->r_faces[i])) return RKL_EINVAL;
     if (i > 0 && !(g->r_faces[i] > g->r_faces[i - 1])) return RKL_EINVAL;
@@ -222,6 +223,7 @@ int rkl_create(rkl_ctx **out, const rkl_grid *g, int prec, void *stream) {
   ctx->d.nrt = (long long)g->nr * g->nth;
   ctx->d.N = ctx->d.nrt * g->nph;
   ctx->rf.assign(g->r_faces, g->r_faces + g->nr + 1);
+  if (g->rsun_cm > 0.0) ctx->rsun_cm = g->rsun_cm;
   ctx->stream = (cudaStream_t)stream;
   ctx->prec = prec;
   int rc = cuda_check(ctx, cudaGetDevice(&ctx->device), "cudaGetDevice");

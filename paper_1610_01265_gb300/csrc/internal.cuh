@@ -18,7 +18,7 @@
 
 #include "../../include/rklpcg.h"
 
-#define RKL_RSUN_CM 6.96e10
+#define RKL_RSUN_CM 6.96e10  // default length unit of the radial faces (rkl_grid.rsun_cm = 0)
 #define RKL_KBOLTZ 1.380649e-16
 #define RKL_TCUT 5.0e5
 #define RKL_PI 3.14159265358979323846
@@ -119,6 +119,7 @@ struct rkl_ctx {
   cudaStream_t stream;
   std::string err;
   std::vector<double> rf;
+  double rsun_cm = RKL_RSUN_CM;  // length unit of rf (cm)
   int nsm;
 
   // geometry

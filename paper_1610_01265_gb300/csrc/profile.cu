@@ -7,6 +7,9 @@
 // of iterations past convergence return at once; those launches are recognised from the
 // iteration count read back after the chunk and are not counted, so the per-launch
 // average of a kernel is the duration of launches that did the work.
+//
+// rkl_fp64_peak measures the device's FP64 FMA throughput, the roof of the FP64 stencil
+// kernels on this part.
 #include <cuda_runtime.h>
 
 #include "internal.cuh"
@@ -85,9 +88,75 @@ void prof_release(rkl_ctx *ctx) {
   ctx->ev_pool.clear();
 }
 
+namespace {
+
+constexpr int PEAK_CHAINS = 8;    // independent FMA chains per thread
+constexpr int PEAK_THREADS = 256;
+
+// PEAK_CHAINS independent a <- a * b + c chains per thread (b < 1: every chain converges to
+// c / (1 - b), so the values stay finite); the sums are stored so that no chain is dead code.
+__global__ void __launch_bounds__(PEAK_THREADS) k_dfma_peak(int iters, double b, double c, double *out) {
+  double a[PEAK_CHAINS];
+#pragma unroll
+  for (int q = 0; q < PEAK_CHAINS; q++) a[q] = 1e-3 * threadIdx.x + q;
+#pragma unroll 4
+  for (int it = 0; it < iters; it++) {
+#pragma unroll
+    for (int q = 0; q < PEAK_CHAINS; q++) a[q] = fma(a[q], b, c);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int q = 0; q < PEAK_CHAINS; q++) s += a[q];
+  out[(size_t)blockIdx.x * PEAK_THREADS + threadIdx.x] = s;
+}
+
+}  // namespace
+
 }  // namespace rkl
 
 using namespace rkl;
+
+extern "C" int rkl_fp64_peak(void *cuda_stream, double *tflops_out) {
+  if (!tflops_out) return RKL_EINVAL;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1) {
+    cudaGetLastError();
+    return RKL_ECUDA;
+  }
+  const unsigned grid = (unsigned)nsm * 8;  // 8 CTAs of 256 threads per SM
+  const int iters = 16384;
+  double *out = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = RKL_OK;
+  if (cudaMalloc(&out, (size_t)grid * PEAK_THREADS * sizeof(double)) != cudaSuccess || !out) rc = RKL_ENOMEM;
+  if (!rc && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) rc = RKL_ECUDA;
+  float best = 0.0f;
+  if (!rc) {
+    k_dfma_peak<<<grid, PEAK_THREADS, 0, st>>>(iters / 8, 0.999999, 1e-6, out);  // warm-up
+    for (int rep = 0; rep < 3 && !rc; rep++) {
+      cudaEventRecord(e0, st);
+      k_dfma_peak<<<grid, PEAK_THREADS, 0, st>>>(iters, 0.999999, 1e-6, out);
+      cudaEventRecord(e1, st);
+      float ms = 0.0f;
+      if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+        rc = RKL_ECUDA;
+      else if (ms > 0.0f && (best == 0.0f || ms < best))
+        best = ms;
+    }
+  }
+  if (!rc && cudaGetLastError() != cudaSuccess) rc = RKL_ECUDA;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (out) cudaFree(out);
+  cudaGetLastError();
+  if (rc) return rc;
+  if (!(best > 0.0f)) return RKL_ECUDA;
+  const double flop = 2.0 * PEAK_CHAINS * (double)iters * grid * PEAK_THREADS;
+  *tflops_out = flop / (best * 1e-3) / 1e12;
+  return RKL_OK;
+}
 
 extern "C" int rkl_profile_enable(rkl_ctx *ctx, int on) {
   if (!ctx) return RKL_EINVAL;

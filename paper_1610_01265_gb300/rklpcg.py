@@ -37,7 +37,7 @@ RKL_FORCE_ODD = 1
 EXPORTED = ("rkl_create", "rkl_destroy", "rkl_set_stream", "rkl_strerror", "rkl_last_error",
             "rkl_kernel_launches", "rkl2_stage_count", "set_coeffs", "apply_F", "rkl2_superstep",
             "be_pcg_solve", "rkl2_superstep_noalloc", "rkl_profile_enable", "rkl_profile_read",
-            "sts_advance")
+            "sts_advance", "rkl_fp64_peak")
 RKL_SCHEME_RKL2 = 0
 RKL_SCHEME_RKL1 = 1
 
@@ -61,7 +61,7 @@ class StsOptions(ctypes.Structure):
 
 class _Grid(ctypes.Structure):
     _fields_ = [("nr", ctypes.c_int), ("nth", ctypes.c_int), ("nph", ctypes.c_int),
-                ("r_faces", ctypes.POINTER(ctypes.c_double))]
+                ("r_faces", ctypes.POINTER(ctypes.c_double)), ("rsun_cm", ctypes.c_double)]
 
 
 _lib = None
@@ -101,6 +101,7 @@ def load(path: str | None = None):
     lib.rkl_profile_read.argtypes = [P, I, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong)]
     lib.rkl2_superstep_noalloc.argtypes = [ctypes.POINTER(_Grid), P, P, P, D, I, P, D, I, I, P,
                                            ctypes.POINTER(D), ctypes.POINTER(I)]
+    lib.rkl_fp64_peak.argtypes = [P, ctypes.POINTER(D)]
     _lib = lib
     return lib
 
@@ -135,6 +136,15 @@ def rkl2_superstep_noalloc(r_faces, nth: int, nph: int, T, bhat, n, u, dt: float
     if code != RKL_OK:
         raise RklError(code, "rkl2_superstep_noalloc")
     return used.value, dte.value
+
+
+def fp64_peak(stream=None) -> float:
+    """Measured FP64 FMA throughput of the current device, TFLOP/s (instrumentation)."""
+    tf = ctypes.c_double(0.0)
+    code = load().rkl_fp64_peak(stream if stream is not None else _current_stream(), ctypes.byref(tf))
+    if code != RKL_OK:
+        raise RklError(code, "rkl_fp64_peak")
+    return tf.value
 
 
 def _ptr(a, n: int | None = None):
@@ -174,15 +184,16 @@ def _current_stream():
 class Context:
     """One grid on the current CUDA device; mirrors rkl_create .. rkl_destroy."""
 
-    def __init__(self, r_faces, nth: int, nph: int, stream=None, prec: int = RKL_F64):
+    def __init__(self, r_faces, nth: int, nph: int, stream=None, prec: int = RKL_F64, rsun_cm: float = 0.0):
         """prec = RKL_F64, or RKL_F32MIX for the mixed-precision path (FP32 operator and
-        stages, FP64 coefficients of the recurrence, dot products and residual correction)."""
+        stages, FP64 coefficients of the recurrence, dot products and residual correction).
+        rsun_cm: length unit of r_faces in cm (0: R_sun = 6.96e10 cm)."""
         self._lib = load()
         rf = np.ascontiguousarray(r_faces, dtype=np.float64)
         self.nr, self.nth, self.nph = len(rf) - 1, int(nth), int(nph)
         self.N = self.nr * self.nth * self.nph
         self._rf = rf
-        g = _Grid(self.nr, self.nth, self.nph, rf.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        g = _Grid(self.nr, self.nth, self.nph, rf.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(rsun_cm))
         h = ctypes.c_void_p()
         if stream is None:
             stream = _current_stream()
