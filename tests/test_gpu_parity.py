@@ -385,3 +385,25 @@ def test_graphs_interleaved_and_teardown(oracle_mod, R, torch_cuda):
                 x_o, it_o, _, st = O.be_pcg(g, S, W, c["T"], ratio * dte, pc=1, rtol=1e-10)
                 assert code == R.RKL_OK and abs(its[0] - it_o) <= 1
         ctx.close()
+
+
+def test_rsun_cm_scales_the_operator(R, torch_cuda):
+    """rkl_grid.rsun_cm is the length unit of the radial faces: doubling it scales areas by
+    4, spacings by 2 and volumes by 8, so S by 2, W by 8, F = -W^-1 S u by 1/4 and the
+    Gershgorin dt_exp (App. B) by 4."""
+    torch = torch_cuda
+    c = synth.conduction_case(8, 6, 8, seed=2)
+    T, b, n = dev(torch, c["T"]), dev(torch, c["bhat"]), dev(torch, c["n"])
+    u = dev(torch, synth.random_field((8, 6, 8), 4))
+    out = []
+    for rs in (0.0, 2 * 6.96e10):
+        with R.Context(c["rf"], 6, 8, rsun_cm=rs) as ctx:
+            dte = ctx.set_conduction(T, b, n)
+            Fu = torch.empty_like(u)
+            ctx.apply_F(u, Fu)
+            out.append((dte, host(Fu)))
+    assert out[1][0] == pytest.approx(4 * out[0][0], rel=1e-13)
+    assert rel_l2(4 * out[1][1], out[0][1]) <= 1e-13
+    with pytest.raises(R.RklError) as e:
+        R.Context(c["rf"], 6, 8, rsun_cm=-1.0)
+    assert e.value.code == R.RKL_EINVAL
