@@ -6,7 +6,9 @@ benchmark's CPU-baseline leg, never by the product path.  The arithmetic lives i
 (gcc, in-tree under ``oracle/_build``) and marshals numpy arrays through ctypes.
 
 Layout: scalar fields are float64 arrays of shape (nph, nth, nr) (r fastest);
-operators are full 19-slot rows, shape (N, 19), slot s = neighbour at offsets()[s].
+operators are full 24-slot rows, shape (N, 24): slot s < 19 the neighbour at offsets()[s],
+slots 19..23 (pole rows with the across-pole option only) the antipodal cells
+(i + di, j, k + nph/2 + dk) for (di, dk) in pole_offsets().
 """
 from __future__ import annotations
 
@@ -23,7 +25,9 @@ _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-NSLOT = 19
+NSLOT = 24   # slots per stored row
+NS19 = 19    # the 19-point stencil
+NPOLE = 5    # antipodal couplings of a pole cell (across-pole option)
 PC_JACOBI = 1
 PC_BILU0 = 2
 STATUS = {0: "converged", 1: "not converged", 2: "breakdown", -1: "bad arguments"}
@@ -71,6 +75,7 @@ def _load():
             lib.or_bilu0_apply.argtypes = [I, I, I, P, P, I, P, P, P]
             lib.or_be_pcg.argtypes = [I, I, I, P, P, P, P, D, I, P, I, D, I, P, I, P, P]
             lib.or_offsets.argtypes = [P]
+            lib.or_pole_offsets.argtypes = [P, P]
             lib.or_num_threads.restype = I
             lib.or_set_num_threads.argtypes = [I]
             _lib = lib
@@ -107,9 +112,18 @@ class Grid:
 
 
 def offsets() -> np.ndarray:
-    out = np.zeros((NSLOT, 3), dtype=np.int32)
+    """(19, 3) neighbour offsets of the stencil slots."""
+    out = np.zeros((NS19, 3), dtype=np.int32)
     _load().or_offsets(_ptr(out))
     return out
+
+
+def pole_offsets() -> np.ndarray:
+    """(5, 2) offsets (di, dk) of the antipodal slots 19..23 from (i, k + nph/2)."""
+    di = np.zeros(NPOLE, dtype=np.int32)
+    dk = np.zeros(NPOLE, dtype=np.int32)
+    _load().or_pole_offsets(_ptr(di), _ptr(dk))
+    return np.stack([di, dk], axis=1)
 
 
 def num_threads() -> int:
@@ -122,17 +136,18 @@ def set_num_threads(n: int) -> None:
 
 
 def assemble_conduction(g: Grid, T, bhat, n, kappa0: float = 9e-7, beta_tcut: bool = False,
-                        isotropic: bool = False, flux_form: bool = False):
-    """S (N,19) = Hessian of the discrete energy (flux_form: minus the divergence of the
-    face fluxes, non-symmetric, whose symmetric part is that Hessian), W (N,) = 3 k_B n V."""
+                        isotropic: bool = False, flux_form: bool = False, across_pole: bool = False):
+    """S (N,24) = Hessian of the discrete energy (flux_form: minus the divergence of the
+    face fluxes, non-symmetric, whose symmetric part is that Hessian), W (N,) = 3 k_B n V.
+    across_pole: theta-ghosts beyond a pole at phi + pi (needs nth >= 2, even nph >= 6)."""
     T, bhat, n = _f64(T), _f64(bhat), _f64(n)
     S = np.empty((g.N, NSLOT))
     W = np.empty(g.N)
-    flags = (1 if beta_tcut else 0) | (2 if isotropic else 0) | (4 if flux_form else 0)
+    flags = (1 if beta_tcut else 0) | (2 if isotropic else 0) | (4 if flux_form else 0) | (8 if across_pole else 0)
     rc = _load().or_assemble_conduction(*g._dims(), _ptr(T), _ptr(bhat), _ptr(n), kappa0, flags,
                                         _ptr(S), _ptr(W))
     if rc != 0:
-        raise ValueError("bad grid for the oracle (needs nr>=1, nth>=1, nph>=3)")
+        raise ValueError("bad grid for the oracle (needs nr>=1, nth>=1, nph>=3; across-pole: nth>=2, even nph>=6)")
     return S, W
 
 
@@ -147,9 +162,9 @@ def assemble_viscosity(g: Grid, rho, nu):
 
 
 def energy_conduction(g: Grid, T, bhat, n, u, kappa0: float = 9e-7, beta_tcut: bool = False,
-                      isotropic: bool = False) -> float:
+                      isotropic: bool = False, across_pole: bool = False) -> float:
     T, bhat, n, u = _f64(T), _f64(bhat), _f64(n), _f64(u)
-    flags = (1 if beta_tcut else 0) | (2 if isotropic else 0)
+    flags = (1 if beta_tcut else 0) | (2 if isotropic else 0) | (8 if across_pole else 0)
     return _load().or_energy_conduction(*g._dims(), _ptr(T), _ptr(bhat), _ptr(n), kappa0, flags,
                                         _ptr(u))
 
@@ -258,9 +273,10 @@ def be_pcg(g: Grid, S, W, u, dt: float, pc: int = PC_JACOBI, block=(8, 8, 8), rt
     return x, it.value, rel.value, st
 
 
-def dense(g: Grid, S19) -> np.ndarray:
-    """Dense N x N matrix of a 19-slot operator (tiny grids only)."""
+def dense(g: Grid, S) -> np.ndarray:
+    """Dense N x N matrix of a stored operator (tiny grids only)."""
     off = offsets()
+    poff = pole_offsets()
     N = g.N
     Dm = np.zeros((N, N))
     nr, nth, nph = g.nr, g.nth, g.nph
@@ -268,8 +284,13 @@ def dense(g: Grid, S19) -> np.ndarray:
         for j in range(nth):
             for i in range(nr):
                 c = (k * nth + j) * nr + i
-                for s in range(NSLOT):
+                for s in range(NS19):
                     ii, jj, kk = i + off[s, 0], j + off[s, 1], (k + off[s, 2]) % nph
                     if 0 <= ii < nr and 0 <= jj < nth:
-                        Dm[c, (kk * nth + jj) * nr + ii] += S19[c, s]
+                        Dm[c, (kk * nth + jj) * nr + ii] += S[c, s]
+                if j in (0, nth - 1):
+                    for q in range(NPOLE):
+                        ii, kk = i + poff[q, 0], (k + nph // 2 + poff[q, 1]) % nph
+                        if 0 <= ii < nr:
+                            Dm[c, (kk * nth + j) * nr + ii] += S[c, NS19 + q]
     return Dm

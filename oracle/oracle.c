@@ -41,11 +41,16 @@
  * r faces at r = r_min and r = r_max are omitted (zero flux); pole faces have zero
  * area.  Transverse neighbours beyond r or theta boundaries are mirror ghosts equal
  * to the cell itself (ghost centre mirrored through the boundary face); phi is
- * periodic.  Viscosity: Q_v = 1/2 sum_f Vt_f mu_f g_f^2, mu = nu rho, per Cartesian
+ * periodic.  With the across-pole option (Sec. 4.2 boundaries: a theta-difference next
+ * to a pole taken across it) the theta-neighbour beyond a pole is instead the cell of
+ * the same pole row half a revolution away, at phi + pi (the meridian continued
+ * through the pole), which couples a pole cell to five cells of the antipodal column.
+ * Viscosity: Q_v = 1/2 sum_f Vt_f mu_f g_f^2, mu = nu rho, per Cartesian
  * component, W = rho V.
  *
- * Storage: a symmetric operator S is kept as full rows of 19 slots, S[c*19 + s],
- * slot s meaning the neighbour at offset OFF[s] (phi wrapped).
+ * Storage: an operator S is kept as full rows of 24 slots, S[c*24 + s]: slot s < 19
+ * the neighbour at offset OFF[s] (phi wrapped); slots 19..23, used by pole rows with the
+ * across-pole option only, the antipodal cells (i + PDI[q], j, k + nph/2 + PDK[q]).
  */
 #include <math.h>
 #include <stdlib.h>
@@ -58,9 +63,16 @@
 #define OR_KB 1.380649e-16
 #define OR_PI 3.14159265358979323846
 #define OR_TCUT 5.0e5
-#define NS 19
+#define NS19 19
+#define NPOLE 5
+#define NS (NS19 + NPOLE)
 
-static const int OFF[NS][3] = {
+/* antipodal couplings of a pole cell (i, j, k) with the across-pole option: the cells
+   (i + PDI[q], j, k + nph/2 + PDK[q]) of the same pole row */
+static const int PDI[NPOLE] = {0, 1, -1, 0, 0};
+static const int PDK[NPOLE] = {0, 0, 0, 1, -1};
+
+static const int OFF[NS19][3] = {
     {0, 0, 0},
     {-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1},
     {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}, {1, 1, 0},
@@ -70,9 +82,15 @@ static const int OFF[NS][3] = {
 typedef struct {
   int nr, nth, nph;
   const double *rf;
+  int pole; /* across-pole theta-ghosts (needs nth >= 2 and nph even, >= 6) */
 } grid;
 
 void or_offsets(int *out) { memcpy(out, OFF, sizeof(OFF)); }
+void or_pole_offsets(int *di, int *dk) {
+  memcpy(di, PDI, sizeof(PDI));
+  memcpy(dk, PDK, sizeof(PDK));
+}
+static int pole_row(const grid *g, int j) { return j == 0 || j == g->nth - 1; }
 
 int or_num_threads(void) {
 #ifdef _OPENMP
@@ -141,15 +159,21 @@ static double cdiff_dist(const grid *g, int b, int i, int j) {
 }
 
 /* neighbour of (i,j,k) one step along direction b with sign sg, mirror ghosts in r and
-   theta (the ghost is the cell itself), periodic in phi */
+   theta (the ghost is the cell itself), periodic in phi; with the across-pole option the
+   theta-step beyond a pole lands on the cell at phi + pi of the same row */
 static void remap(const grid *g, int i, int j, int k, int b, int sg, int *o) {
   o[0] = i; o[1] = j; o[2] = k;
   if (b == 0) { int n = i + sg; if (n >= 0 && n < g->nr) o[0] = n; }
-  else if (b == 1) { int n = j + sg; if (n >= 0 && n < g->nth) o[1] = n; }
+  else if (b == 1) {
+    int n = j + sg;
+    if (n >= 0 && n < g->nth) o[1] = n;
+    else if (g->pole) o[2] = wrapk(g, k + g->nph / 2);
+  }
   else o[2] = wrapk(g, k + sg);
 }
 
-/* slot of cell q relative to cell p; -1 if not in the 19-point stencil */
+/* slot of cell q relative to cell p; -1 if not in the 19-point stencil (nor, for a
+   pole row with the across-pole option, among the five antipodal couplings) */
 static int slot_of(const grid *g, const int *p, const int *q) {
   int d[3];
   d[0] = q[0] - p[0];
@@ -157,13 +181,22 @@ static int slot_of(const grid *g, const int *p, const int *q) {
   d[2] = q[2] - p[2];
   if (d[2] == g->nph - 1) d[2] = -1;
   if (d[2] == -(g->nph - 1)) d[2] = 1;
-  for (int s = 0; s < NS; s++)
+  for (int s = 0; s < NS19; s++)
     if (OFF[s][0] == d[0] && OFF[s][1] == d[1] && OFF[s][2] == d[2]) return s;
+  if (g->pole && d[1] == 0 && pole_row(g, p[1]))
+    for (int q5 = 0; q5 < NPOLE; q5++)
+      if (d[0] == PDI[q5] && wrapk(g, q[2] - p[2] - g->nph / 2 - PDK[q5]) == 0) return NS19 + q5;
   return -1;
 }
 
-/* neighbour cell index of slot s, or -1 if outside r/theta range */
+/* neighbour cell index of slot s, or -1 if outside r/theta range (the antipodal slots
+   s >= 19 exist for pole rows only) */
 static long nbr(const grid *g, int i, int j, int k, int s) {
+  if (s >= NS19) {
+    int ii = i + PDI[s - NS19];
+    if (!pole_row(g, j) || ii < 0 || ii >= g->nr) return -1;
+    return cidx(g, ii, j, wrapk(g, k + g->nph / 2 + PDK[s - NS19]));
+  }
   int ii = i + OFF[s][0], jj = j + OFF[s][1];
   if (ii < 0 || ii >= g->nr || jj < 0 || jj >= g->nth) return -1;
   return cidx(g, ii, jj, wrapk(g, k + OFF[s][2]));
@@ -203,18 +236,20 @@ static int face_cells(const grid *g, int a, int i, int j, int k, int *L, int *R)
 }
 
 /*
- * Conduction: assemble S = Hessian of Q (19 slots per row, zeroed here) and
+ * Conduction: assemble S = Hessian of Q (24 slots per row, zeroed here) and
  * W = 3 k_B n V.  flags: bit0 = beta_Tcut, bit1 = isotropic test hook (bhat bhat^T -> I),
  * bit2 = flux form: row c is minus the divergence of the face fluxes
  * A_f (D_f^aa g_f + sum_{b!=a} D_f^ab ghat_b(f)) through the faces of c, the "standard"
  * non-symmetric scheme whose symmetric part is the Hessian of Q (Sec. 4.2; PCG is used
- * for such slightly non-symmetric operators, Sec. 2.1).
+ * for such slightly non-symmetric operators, Sec. 2.1); bit3 = across-pole theta-ghosts
+ * (needs nth >= 2 and an even nph >= 6).
  */
 int or_assemble_conduction(int nr, int nth, int nph, const double *rf, const double *T,
                            const double *bhat, const double *n, double kappa0, int flags,
                            double *S, double *W) {
-  grid g = {nr, nth, nph, rf};
+  grid g = {nr, nth, nph, rf, (flags & 8) != 0};
   if (nr < 1 || nth < 1 || nph < 3) return -1;
+  if (g.pole && (nth < 2 || nph < 6 || nph % 2)) return -1;
   long N = ncell(&g);
   memset(S, 0, sizeof(double) * NS * N);
   for (int k = 0; k < nph; k++)
@@ -281,7 +316,7 @@ int or_assemble_conduction(int nr, int nth, int nph, const double *rf, const dou
 double or_energy_conduction(int nr, int nth, int nph, const double *rf, const double *T,
                             const double *bhat, const double *n, double kappa0, int flags,
                             const double *u) {
-  grid g = {nr, nth, nph, rf};
+  grid g = {nr, nth, nph, rf, (flags & 8) != 0};
   long N = ncell(&g);
   (void)n;
   double Q = 0.0;
@@ -321,7 +356,7 @@ double or_energy_conduction(int nr, int nth, int nph, const double *rf, const do
    mu = nu rho, mu_f = (mu_L + mu_R)/2, W = rho V. */
 int or_assemble_viscosity(int nr, int nth, int nph, const double *rf, const double *rho,
                           const double *nu, double *S, double *W) {
-  grid g = {nr, nth, nph, rf};
+  grid g = {nr, nth, nph, rf, 0};
   if (nr < 1 || nth < 1 || nph < 3) return -1;
   long N = ncell(&g);
   memset(S, 0, sizeof(double) * NS * N);
@@ -367,7 +402,7 @@ static void s_apply(const grid *g, const double *S, const double *u, double *out
 
 int or_apply_F(int nr, int nth, int nph, const double *rf, const double *S, const double *W,
                const double *u, double *Fu) {
-  grid g = {nr, nth, nph, rf};
+  grid g = {nr, nth, nph, rf, 0};
   long N = ncell(&g);
   s_apply(&g, S, u, Fu);
 #pragma omp parallel for schedule(static)
@@ -378,7 +413,7 @@ int or_apply_F(int nr, int nth, int nph, const double *rf, const double *S, cons
 /* ---------------- App. B: Gershgorin bound on |lambda|max of M ---------------- */
 double or_gershgorin_dt(int nr, int nth, int nph, const double *rf, const double *S,
                         const double *W, double *lam_out) {
-  grid g = {nr, nth, nph, rf};
+  grid g = {nr, nth, nph, rf, 0};
   long N = ncell(&g);
   double lam = 0.0;
   for (long c = 0; c < N; c++) {
@@ -420,7 +455,7 @@ void or_rkl2_coeffs(int s, double *mu, double *nu, double *mut, double *gt) {
 
 int or_rkl2_superstep(int nr, int nth, int nph, const double *rf, const double *S,
                       const double *W, double *u, double dt, int s) {
-  grid g = {nr, nth, nph, rf};
+  grid g = {nr, nth, nph, rf, 0};
   long N = ncell(&g);
   if (s < 2) return -1;
   double *mu = malloc(sizeof(double) * (s + 1)), *nu = malloc(sizeof(double) * (s + 1));
@@ -476,7 +511,7 @@ void or_rkl1_coeffs(int s, double *mu, double *nu, double *mut) {
 
 int or_rkl1_superstep(int nr, int nth, int nph, const double *rf, const double *S,
                       const double *W, double *u, double dt, int s) {
-  grid g = {nr, nth, nph, rf};
+  grid g = {nr, nth, nph, rf, 0};
   long N = ncell(&g);
   if (s < 1) return -1;
   double *mu = malloc(sizeof(double) * (s + 1)), *nu = malloc(sizeof(double) * (s + 1));
@@ -520,6 +555,7 @@ static int g_npat = 19;
 /* is the slot-s neighbour of (i,j,k) inside the same block (no phi wrap) and in the
    operator's pattern? */
 static int in_block(const grid *g, const int *blk, int i, int j, int k, int s) {
+  if (s >= NS19) return 0; /* antipodal couplings: dropped like those across the phi seam */
   int ii = i + OFF[s][0], jj = j + OFF[s][1], kk = k + OFF[s][2];
   (void)g;
   if (g_npat == 7 && s >= 7) return 0;
@@ -548,7 +584,7 @@ static int block_row(const grid *g, const int *blk, int i, int j, int k, int *sl
   return m;
 }
 static int slot_by_offset(int di, int dj, int dk) {
-  for (int s = 0; s < NS; s++)
+  for (int s = 0; s < NS19; s++)
     if (OFF[s][0] == di && OFF[s][1] == dj && OFF[s][2] == dk) return s;
   return -1;
 }
@@ -557,7 +593,7 @@ static int slot_by_offset(int di, int dj, int dk) {
    only slots inside the block are meaningful (others are set to zero). */
 int or_bilu0_factor(int nr, int nth, int nph, const double *rf, const int *blk, int npat,
                     const double *A, double *LU) {
-  grid g = {nr, nth, nph, rf};
+  grid g = {nr, nth, nph, rf, 0};
   if (npat != 19 && npat != 7) return -1;
   g_npat = npat;
   long N = ncell(&g);
@@ -603,7 +639,7 @@ int or_bilu0_factor(int nr, int nth, int nph, const double *rf, const int *blk, 
 
 int or_bilu0_apply(int nr, int nth, int nph, const double *rf, const int *blk, int npat,
                    const double *LU, const double *r, double *z) {
-  grid g = {nr, nth, nph, rf};
+  grid g = {nr, nth, nph, rf, 0};
   if (npat != 19 && npat != 7) return -1;
   g_npat = npat;
   int nbk = nph / blk[2], nbj = nth / blk[1], nbi = nr / blk[0];
@@ -660,7 +696,7 @@ static double dot(long N, const double *a, const double *b) {
 int or_be_pcg(int nr, int nth, int nph, const double *rf, const double *S, const double *W,
               double *u, double dt, int pc, const int *blk, int npat, double rtol, int maxit,
               const double *x0, int fixed_iters, int *iters_out, double *relres_out) {
-  grid g = {nr, nth, nph, rf};
+  grid g = {nr, nth, nph, rf, 0};
   long N = ncell(&g);
   if (pc != 1 && pc != 2) return -1;
   if (npat != 19 && npat != 7) return -1;
