@@ -57,8 +57,9 @@ FP64_PEAK_TFLOPS = 1.25  # nominal FP64 rate of the GB300 (2 DFMA/clk/SM x 152 S
 #  spmv cond: y = A p with A = W + dt S assembled once per solve: 19 FMA + p.y = 40 flop;
 #             10 coefficients of A + p + y = 96 B
 #  spmv visc: 7 FMA + p.y = 16 flop; 4 coefficients + p + y = 48 B
-#  bilu_apply cond: 9 + 9 FMA + 1/U_ii + r.z, r.r = 41 flop; 19 factors + r + z = 168 B
-#  bilu_apply visc: 3 + 3 FMA + 1 + 4 = 17 flop; 7 factors + r + z = 72 B
+#  bilu_apply cond: 9 + 9 FMA + 1/U_ii + r.z = 39 flop; 19 factors + r + z = 168 B
+#                   (r.r is formed by the x, r update that precedes it)
+#  bilu_apply visc: 3 + 3 FMA + 1 + 2 = 15 flop; 7 factors + r + z = 72 B
 KERNEL_COST = {
     ("conduction", "rkl2_stage"): (48.0, 128.0, "alu", "rkl2_stage_128x192x384.md",
                                    ("rkl2.cu:k_rkl2_stage", "stencil.cuh")),
@@ -66,8 +67,8 @@ KERNEL_COST = {
                                   ("rkl2.cu:k_rkl2_stage", "stencil.cuh")),
     ("conduction", "spmv"): (40.0, 96.0, "alu", "spmv_128x192x384.md", ("pcg.cu:k_spmv_a", "stencil.cuh")),
     ("viscosity", "spmv"): (16.0, 48.0, "alu", "spmv_visc_128x192x384.md", ("pcg.cu:k_spmv_a", "stencil.cuh")),
-    ("conduction", "bilu_apply"): (41.0, 168.0, "alu", "bilu_apply_128x192x384.md", ("pcg.cu:k_bilu_apply",)),
-    ("viscosity", "bilu_apply"): (17.0, 72.0, "alu", "bilu_apply_visc_128x192x384.md", ("pcg.cu:k_bilu_apply",)),
+    ("conduction", "bilu_apply"): (39.0, 168.0, "alu", "bilu_apply_128x192x384.md", ("pcg.cu:k_bilu_apply",)),
+    ("viscosity", "bilu_apply"): (15.0, 72.0, "alu", "bilu_apply_visc_128x192x384.md", ("pcg.cu:k_bilu_apply",)),
 }
 # part of the demangled ncu kernel name of each family (for --summarize-ncu)
 FAMILY_KERNEL = {

@@ -73,6 +73,7 @@ enum { RKL_F64 = 0, RKL_F32MIX = 1 };
 
 #define RKL_BETA_TCUT 1 /* set_coeffs: kappa times (T / 5e5 K)^{5/2} below 5e5 K (Sec. 4.1 beta_Tcut) */
 #define RKL_FLUX_FORM 2 /* set_coeffs (conduction): non-symmetric flux form, see set_coeffs */
+#define RKL_ACROSS_POLE 4 /* set_coeffs (conduction): theta-ghosts beyond a pole at phi + pi, see set_coeffs */
 #define RKL_FORCE_ODD 1 /* rkl2_superstep: round s up to an odd number (Sec. 3) */
 
 /* Create a context for one grid on the current CUDA device.
@@ -152,8 +153,21 @@ int rkl2_stage_count(double dt_over_dt_exp, int flags);
  *        stored as full 19-entry rows (152 B per cell instead of 80).  Every solver
  *        accepts it; PCG then runs as for "slightly non-symmetric" operators (Sec. 2.1)
  *        and still stops on the true residual.  rkl2_superstep_noalloc does not.
+ *        With RKL_ACROSS_POLE (symmetric form only; needs nth >= 2 and an even
+ *        nph >= 6, else RKL_EINVAL) the theta-difference of a cell next to a pole is
+ *        taken across the pole (Sec. 4.2 boundaries): its ghost is the cell of the same
+ *        row at phi + pi instead of the cell itself, which makes the difference a centred
+ *        one along the meridian continued through the pole (consistent there, where the
+ *        mirror ghost is not) and couples each pole cell to five cells of the antipodal
+ *        column.  S stays symmetric with zero row sums; it is no longer positive
+ *        semi-definite to rounding: one or two eigenvalues are slightly negative (about
+ *        -1e-5 of the largest at 6 theta rows, -1e-7 at 24), so RKL2 lets those modes grow
+ *        by about exp(|lambda| dt) per step and BE stays definite while dt |lambda| is
+ *        below the smallest W.  The block-ILU0 preconditioner drops the across-pole
+ *        couplings (they leave every block, like those across the phi seam).
  *   op = RKL_OP_VISCOSITY:  a = rho [N] (g cm^-3), b = NULL, c = nu [N] (cm^2/s);
- *        kappa0 is ignored; RKL_FLUX_FORM is RKL_EINVAL, other flags are ignored.
+ *        kappa0 is ignored; RKL_FLUX_FORM is RKL_EINVAL, other flags are ignored
+ *        (the 7-point viscosity operator has no transverse differences).
  * dt_exp_out (host, may be NULL) receives dt_exp in seconds.  Invalidates any
  * cached preconditioner.  RKL_ENONFINITE if an input is NaN/Inf or T, n, rho, nu <= 0. */
 int set_coeffs(rkl_ctx *ctx, int op, const double *a, const double *b, const double *c,
@@ -196,8 +210,9 @@ int sts_advance(rkl_ctx *ctx, double *u, int ncomp, double dt, double dt_exp,
  * ||r||_2 <= rtol ||W u||_2 (tested after r.z as in Fig. 1) or after maxit
  * products A p.  pc = RKL_PC_JACOBI (PC1) or RKL_PC_BILU0 (PC2: zero-fill ILU of
  * every block[0] x block[1] x block[2] sub-domain, couplings between blocks and
- * across the phi seam dropped, App. A); block is ignored for PC1 and the grid must
- * be divisible by it for PC2.  rtol <= 0 runs exactly maxit iterations.
+ * across the phi seam dropped, App. A); block is ignored for PC1.  For PC2 the grid
+ * must be divisible by the block, which holds at most 4096 cells (else RKL_EINVAL).
+ * rtol <= 0 runs exactly maxit iterations.
  * iters_out / relres_out (host, may be NULL) receive ncomp values each: the number
  * of A p products and the final ||r||/||W u||.  Returns RKL_ENOTCONV if some
  * component did not converge, RKL_EBREAKDOWN on p.Ap <= 0. */
@@ -217,7 +232,7 @@ int be_pcg_solve(rkl_ctx *ctx, double *u, int ncomp, double dt, int pc, const in
  * hence nr <= 1024, nth <= 1024 and nr*nth*nph <= 65536 cells (RKL_EINVAL beyond).
  * T [N], bhat [3N], n [N] and u [N] must be device pointers (RKL_EINVAL otherwise); u is
  * advanced in place.  kappa0 and coeff_flags are those of set_coeffs (RKL_BETA_TCUT
- * only: RKL_FLUX_FORM is RKL_EINVAL); dt and flags are those of rkl2_superstep; s > 0
+ * only: RKL_FLUX_FORM and RKL_ACROSS_POLE are RKL_EINVAL); dt and flags are those of rkl2_superstep; s > 0
  * runs exactly s stages, s == 0 the stage count that rkl2_stage_count gives for dt over
  * the dt_exp computed here.  dt_exp_out and s_used (host, may be NULL) receive dt_exp and
  * the number of stages.

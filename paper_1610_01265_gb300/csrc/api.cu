@@ -230,7 +230,9 @@ int rkl_create(rkl_ctx **out, const rkl_grid *g, int prec, void *stream) {
   if (!rc) rc = cuda_check(ctx, cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, ctx->device), "SM count");
   if (!rc) rc = build_geometry(ctx);
   const size_t N = (size_t)ctx->d.N;
-  if (!rc) rc = cuda_check(ctx, cudaMalloc(&ctx->coef, NCOEF_COND * N * sizeof(double)), "alloc coefficients");
+  if (!rc)
+    rc = cuda_check(ctx, cudaMalloc(&ctx->coef, (NCOEF_COND * N + pole_extra(ctx->d)) * sizeof(double)),
+                    "alloc coefficients");
   if (!rc) ctx->coef_slots = NCOEF_COND;
   if (!rc) rc = cuda_check(ctx, cudaMalloc(&ctx->W, N * sizeof(double)), "alloc W");
   if (!rc) rc = cuda_check(ctx, cudaMalloc(&ctx->invW, N * sizeof(double)), "alloc 1/W");
@@ -314,8 +316,13 @@ int set_coeffs(rkl_ctx *ctx, int op, const double *a, const double *b, const dou
     return set_error(ctx, RKL_EINVAL, "set_coeffs: kappa0 must be finite and > 0");
   if (op == RKL_OP_VISCOSITY && (flags & RKL_FLUX_FORM))
     return set_error(ctx, RKL_EINVAL, "set_coeffs: the flux form is a conduction option");
+  const bool pole = op == RKL_OP_CONDUCTION && (flags & RKL_ACROSS_POLE);
+  if (pole && (flags & RKL_FLUX_FORM))
+    return set_error(ctx, RKL_EINVAL, "set_coeffs: across-pole ghosts are built for the symmetric form only");
+  if (pole && (ctx->d.nth < 2 || ctx->d.nph < 6 || ctx->d.nph % 2))
+    return set_error(ctx, RKL_EINVAL, "set_coeffs: across-pole ghosts need nth >= 2 and an even nph >= 6");
   const size_t N = (size_t)ctx->d.N;
-  const int kind = (op == RKL_OP_CONDUCTION && (flags & RKL_FLUX_FORM)) ? OPK_FLUX : op;
+  const int kind = (op == RKL_OP_CONDUCTION && (flags & RKL_FLUX_FORM)) ? OPK_FLUX : (pole ? OPK_POLE : op);
   ctx->op = -1;
   ctx->lu_valid = 0;
   ctx->acoef_valid = 0;
@@ -327,7 +334,8 @@ int set_coeffs(rkl_ctx *ctx, int op, const double *a, const double *b, const dou
     cudaFree(ctx->coef);
     ctx->coef = nullptr;
     ctx->coef_slots = 0;
-    if ((rc = cuda_check(ctx, cudaMalloc(&ctx->coef, op_ncoef(kind) * N * sizeof(double)), "alloc coefficients")))
+    if ((rc = cuda_check(ctx, cudaMalloc(&ctx->coef, (op_ncoef(kind) * N + pole_extra(ctx->d)) * sizeof(double)),
+                         "alloc coefficients")))
       return rc;
     ctx->coef_slots = op_ncoef(kind);
   }
@@ -374,10 +382,12 @@ int set_coeffs(rkl_ctx *ctx, int op, const double *a, const double *b, const dou
       ctx->coef32 = nullptr;
     }
     if (!ctx->coef32) ctx->coef32_slots = (int)std::max<long long>(nslot, NCOEF_COND);
-    if ((rc = ensure_fbuffer(ctx, &ctx->coef32, (size_t)ctx->coef32_slots * N, "alloc FP32 coefficients")) ||
+    const long long nconv = nslot * (long long)N + (kind == OPK_POLE ? pole_extra(ctx->d) : 0);
+    if ((rc = ensure_fbuffer(ctx, &ctx->coef32, (size_t)ctx->coef32_slots * N + pole_extra(ctx->d),
+                             "alloc FP32 coefficients")) ||
         (rc = ensure_fbuffer(ctx, &ctx->W32, N, "alloc FP32 W")) ||
         (rc = ensure_fbuffer(ctx, &ctx->invW32, N, "alloc FP32 1/W")) ||
-        (rc = launch_to_float(ctx, ctx->coef, ctx->coef32, nslot * (long long)N)) ||
+        (rc = launch_to_float(ctx, ctx->coef, ctx->coef32, nconv)) ||
         (rc = launch_to_float(ctx, ctx->W, ctx->W32, (long long)N)) ||
         (rc = launch_to_float(ctx, ctx->invW, ctx->invW32, (long long)N))) {
       ctx->op = -1;

@@ -230,7 +230,64 @@ __device__ __forceinline__ void faces_of_direction(double (&row)[27], const RowC
   trans_face<A, 1, -1, 1>(row, C, g, FS, N);
 }
 
-template <int FLUX>
+// Across-pole theta-ghosts (POLE): in the pole rows j0 = 0 (sigma = +1) and nth - 1
+// (sigma = -1) the centred theta-difference G(X) of a cell X gains sigma (u_X - u_Xb) / d,
+// d = 2 r_i dtheta, Xb the cell at phi + pi, over the mirror ghost.  With
+// beta_f = Vt D^{a theta} / (2h) of an r- or phi-face f = (L, R) of the pole row the energy
+// changes by 1/2 sigma beta_f (u_R - u_L) [(u_L - u_Lb)/d_L + (u_R - u_Rb)/d_R], whose
+// Hessian adds, with gam_i = 1/(2 d_i):
+//   diagonal        -2 A(X),  A(Y) = sigma gam_i (br(i,kY) + bp(i,kY) - br(i-1,kY) - bp(i,kY-1))
+//   towards X + e_r  sigma br(i,k) (gam_i - gam_{i+1})         (towards X + e_phi: nothing)
+//   antipodal (0, 0)     A(X) + A(Xb)
+//             (+1, 0)    sigma br(i,k) gam_{i+1} - sigma br(i,kb) gam_i
+//             (-1, 0)  -sigma br(i-1,k) gam_{i-1} + sigma br(i-1,kb) gam_i
+//             (0, +1)    sigma bp(i,k) gam_i - sigma bp(i,kb) gam_i
+//             (0, -1)  -sigma bp(i,k-1) gam_i + sigma bp(i,kb-1) gam_i
+// (br, bp: beta of the r-face i -> i+1 and of the phi-face k -> k+1 in the pole row,
+// zero where there is no face).  Each antipodal entry is the sum of a term from X's faces
+// and one from Xb's, computed by the same expressions in both rows, so S stays exactly
+// symmetric.
+struct PoleRow {
+  double diag, fwd_r, bwd_r;  // changes of the diagonal and of the entries towards X +- e_r
+  double ap[NPOLE];           // antipodal entries, (di, dk) = (pole_di(q), pole_dk(q))
+};
+
+__device__ __forceinline__ double pole_gam(const Geo &g, int i) { return 0.5 / (2.0 * g.rc[i] * g.dth); }
+
+__device__ PoleRow pole_row(const Dims &d, const Geo &g, const double *__restrict__ FS, int i, int j, int k) {
+  const long long N = d.N;
+  const double sg = j == 0 ? 1.0 : -1.0;
+  const int kb = (k + d.nph / 2) % d.nph;
+  auto cell = [&](int ii, int kk) { return ((long long)kk * d.nth + j) * d.nr + ii; };
+  auto km = [&](int kk) { return kk > 0 ? kk - 1 : d.nph - 1; };
+  auto br = [&](int ii, int kk) { return ii < 0 ? 0.0 : FS[1 * N + cell(ii, kk)]; };  // r-face, theta cross
+  auto bp = [&](int ii, int kk) { return FS[8 * N + cell(ii, kk)]; };                 // phi-face, theta cross
+  const double gi = pole_gam(g, i);
+  auto A = [&](int kk) { return sg * gi * (((br(i, kk) + bp(i, kk)) - br(i - 1, kk)) - bp(i, km(kk))); };
+  PoleRow p;
+  const double a = A(k), ab = A(kb);
+  p.diag = -2.0 * a;
+  p.ap[0] = a + ab;
+  p.fwd_r = 0.0;
+  p.bwd_r = 0.0;
+  p.ap[1] = 0.0;
+  p.ap[2] = 0.0;
+  if (i < d.nr - 1) {
+    const double gp = pole_gam(g, i + 1);
+    p.fwd_r = sg * br(i, k) * (gi - gp);
+    p.ap[1] = sg * br(i, k) * gp - sg * br(i, kb) * gi;
+  }
+  if (i > 0) {
+    const double gm = pole_gam(g, i - 1);
+    p.bwd_r = sg * br(i - 1, k) * (gm - gi);
+    p.ap[2] = -(sg * br(i - 1, k) * gm) + sg * br(i - 1, kb) * gi;
+  }
+  p.ap[3] = sg * bp(i, k) * gi - sg * bp(i, kb) * gi;
+  p.ap[4] = -(sg * bp(i, km(k)) * gi) + sg * bp(i, km(kb)) * gi;
+  return p;
+}
+
+template <int FLUX, int POLE>
 __global__ void __launch_bounds__(BLK) k_assemble_cond_fast(Dims d, Geo g, const double *__restrict__ FS,
                                                             const double *__restrict__ invW,
                                                             double *__restrict__ coef,
@@ -259,6 +316,19 @@ __global__ void __launch_bounds__(BLK) k_assemble_cond_fast(Dims d, Geo g, const
   faces_of_direction<1, FLUX>(row, C, g, FS, d.N);
   faces_of_direction<2, FLUX>(row, C, g, FS, d.N);
   double sum = 0.0;
+  if (POLE && (C.j == 0 || C.j == d.nth - 1)) {
+    const PoleRow p = pole_row(d, g, FS, C.i, C.j, k);
+    row[13] += p.diag;
+    row[r27(1, 0, 0)] += p.fwd_r;
+    row[r27(-1, 0, 0)] += p.bwd_r;
+    const long long stride = 2LL * d.nph * d.nr;
+    const long long e = ((long long)(C.j == 0 ? 0 : 1) * d.nph + k) * d.nr + C.i;
+#pragma unroll
+    for (int q = 0; q < NPOLE; q++) {
+      coef[10 * d.N + q * stride + e] = p.ap[q];
+      sum += fabs(p.ap[q]);
+    }
+  }
 #pragma unroll
   for (int q = 0; q < 27; q++) sum += fabs(row[q]);
 #pragma unroll
@@ -348,11 +418,14 @@ int launch_setup_conduction(rkl_ctx *ctx, const double *T, const double *bhat, c
                                             ctx->invW, ctx->d_flag);
   k_faces_cond<<<grid, BLK, 0, ctx->stream>>>(d, ctx->geo, bhat, kappa, FS);
   if (flags & RKL_FLUX_FORM)
-    k_assemble_cond_fast<1><<<grid, BLK, 0, ctx->stream>>>(d, ctx->geo, FS, ctx->invW, ctx->coef,
-                                                          ctx->d_lammax, ctx->d_flag);
+    k_assemble_cond_fast<1, 0><<<grid, BLK, 0, ctx->stream>>>(d, ctx->geo, FS, ctx->invW, ctx->coef,
+                                                             ctx->d_lammax, ctx->d_flag);
+  else if (flags & RKL_ACROSS_POLE)
+    k_assemble_cond_fast<0, 1><<<grid, BLK, 0, ctx->stream>>>(d, ctx->geo, FS, ctx->invW, ctx->coef,
+                                                             ctx->d_lammax, ctx->d_flag);
   else
-    k_assemble_cond_fast<0><<<grid, BLK, 0, ctx->stream>>>(d, ctx->geo, FS, ctx->invW, ctx->coef,
-                                                          ctx->d_lammax, ctx->d_flag);
+    k_assemble_cond_fast<0, 0><<<grid, BLK, 0, ctx->stream>>>(d, ctx->geo, FS, ctx->invW, ctx->coef,
+                                                             ctx->d_lammax, ctx->d_flag);
   ctx->launches += 3;
   return cuda_check(ctx, cudaGetLastError(), "set_coeffs(conduction) launch");
 }
@@ -364,7 +437,7 @@ int launch_setup_conduction_raw(const Dims &d, const Geo &g, cudaStream_t stream
   unsigned grid = grid_for(d.N, BLK);
   k_cell_cond<<<grid, BLK, 0, stream>>>(d, g, T, bhat, n, kappa0, flags, kappa, W, invW, flag);
   k_faces_cond<<<grid, BLK, 0, stream>>>(d, g, bhat, kappa, FS);
-  k_assemble_cond_fast<0><<<grid, BLK, 0, stream>>>(d, g, FS, invW, coef, lammax, flag);
+  k_assemble_cond_fast<0, 0><<<grid, BLK, 0, stream>>>(d, g, FS, invW, coef, lammax, flag);
   return cudaGetLastError() == cudaSuccess ? RKL_OK : RKL_ECUDA;
 }
 

@@ -39,19 +39,31 @@ __host__ __device__ constexpr int fwd_dk(int m) { return (m == 2 || m >= 5) ? 1 
 enum { NCOEF_COND = 10, NCOEF_VISC = 4, NCOEF_FULL = 19 };
 
 // Operator kinds of a context (template argument OP of the kernels): the two public
-// operators with symmetric storage, and conduction in the non-symmetric flux form
-// (RKL_FLUX_FORM) with full-row storage.
-enum { OPK_COND = RKL_OP_CONDUCTION, OPK_VISC = RKL_OP_VISCOSITY, OPK_FLUX = 2 };
+// operators with symmetric storage, conduction in the non-symmetric flux form
+// (RKL_FLUX_FORM) with full-row storage, and symmetric conduction with across-pole
+// theta-ghosts (RKL_ACROSS_POLE).
+enum { OPK_COND = RKL_OP_CONDUCTION, OPK_VISC = RKL_OP_VISCOSITY, OPK_FLUX = 2, OPK_POLE = 3 };
 
 __host__ __device__ constexpr int op_ncoef(int op) {
   return op == OPK_VISC ? NCOEF_VISC : (op == OPK_FLUX ? NCOEF_FULL : NCOEF_COND);
 }
+
+// Across-pole couplings (OPK_POLE).  With the theta-ghost beyond a pole taken at phi + pi,
+// a cell X = (i, j0, k) of a pole row (j0 = 0 or nth - 1) couples to the five cells
+// (i + PDI[q], j0, k + nph/2 + PDK[q]) of the antipodal column.  Their entries are kept
+// after the 10 symmetric slots, at coef + 10 N, as [q][side][k][i] with side 0 for j0 = 0
+// and 1 for j0 = nth - 1 (full rows: the entry of X towards Y is stored at X and, equal,
+// at Y).  Every coefficient array holds room for them.
+__host__ __device__ constexpr int pole_di(int q) { return q == 1 ? 1 : (q == 2 ? -1 : 0); }
+__host__ __device__ constexpr int pole_dk(int q) { return q == 3 ? 1 : (q == 4 ? -1 : 0); }
+enum { NPOLE = 5 };
 
 // f(std::integral_constant<int, OP>{}) for the operator kind op of a context
 template <typename F>
 inline void op_dispatch(int op, F &&f) {
   if (op == OPK_COND) f(std::integral_constant<int, OPK_COND>{});
   else if (op == OPK_FLUX) f(std::integral_constant<int, OPK_FLUX>{});
+  else if (op == OPK_POLE) f(std::integral_constant<int, OPK_POLE>{});
   else f(std::integral_constant<int, OPK_VISC>{});
 }
 
@@ -60,6 +72,9 @@ struct Dims {
   long long N;
   long long nrt;  // nr * nth (one phi layer)
 };
+
+// doubles (or floats) of the across-pole entries that follow the slots of an operator
+__host__ __device__ inline long long pole_extra(const Dims &d) { return (long long)NPOLE * 2 * d.nr * d.nph; }
 
 // Geometry tables in cm (device pointers); built on the host at rkl_create.
 struct Geo {
@@ -91,11 +106,12 @@ struct PcgState {
 
 enum { PCG_RUNNING = 0, PCG_CONVERGED = 1, PCG_BREAKDOWN = 2, PCG_MAXIT = 3 };
 
-// block-ILU0 level schedule of one block shape (device pointers).  G blocks are
-// solved together by one CTA; their factors are stored group by group as
+// block-ILU0 level schedule of one block shape and coupling pattern (device pointers).
+// G blocks are solved together by one CTA; their factors are stored group by group as
 // [slot][G * bs] with the cells of one wavefront of all G blocks contiguous.
 struct IluPlan {
   int bi, bj, bk, bs;     // block dims and cells per block
+  int pat;                // coupling pattern kept by the factorisation: 19 or 7 points
   int nlev;               // number of wavefront levels
   int nbi, nbj, nbk;      // blocks along r, theta, phi
   int nblocks, G, ngroups;
@@ -104,7 +120,20 @@ struct IluPlan {
   const int *pos_of;      // [bs] level-order position of a block-local index
 };
 
-enum { ILU_SLOTS = 20 };  // 0 U_ii, 1..9 L (lower), 10..18 U (upper), 19 1/U_ii
+// wavefront of a block-local cell: li + 2 lj + 3 lk for the 19-point pattern (each of its
+// nine lower neighbours, (1,-1,0) and (0,1,-1) included, lies on an earlier wavefront),
+// li + lj + lk for the 7-point one
+__host__ __device__ constexpr int ilu_level(int pat, int li, int lj, int lk) {
+  return pat == 7 ? li + lj + lk : li + 2 * lj + 3 * lk;
+}
+// factor slots per cell: 19-point 0 U_ii, 1..9 L (lower), 10..18 U (upper), 19 1/U_ii;
+// 7-point 0 U_ii, 1..3 L, 4..6 U, 7 1/U_ii.  lu_slot maps the generic slot s (0 diagonal,
+// 1 + m the lower coupling -FWD[m], 10 + m the upper +FWD[m], 19 the inverse) to the
+// stored one, -1 where the pattern has none.
+__host__ __device__ constexpr int ilu_nslots(int pat) { return pat == 7 ? 8 : 20; }
+__host__ __device__ constexpr int lu_slot(int pat, int s) {
+  return pat != 7 ? s : (s <= 3 ? s : (s >= 10 && s <= 12 ? s - 6 : (s == 19 ? 7 : -1)));
+}
 
 }  // namespace rkl
 
@@ -130,6 +159,7 @@ struct rkl_ctx {
   int op = -1;  // operator kind (OPK_*) once set_coeffs succeeded
   double dt_exp = 0.0;
   double *coef = nullptr;   // coef_slots * N (NCOEF_COND at create, NCOEF_FULL for the flux form)
+                            // + pole_extra (across-pole entries at coef + 10 N)
   int coef_slots = 0;
   double *W = nullptr;      // N
   double *invW = nullptr;   // N

@@ -116,7 +116,7 @@ extern "C" int rkl2_superstep_noalloc(const rkl_grid *g, const double *T, const 
   if (!T || !bhat || !n || !u) return RKL_EINVAL;
   if (!(std::isfinite(kappa0) && kappa0 > 0.0) || !(std::isfinite(dt) && dt > 0.0)) return RKL_EINVAL;
   if (s < 0 || s == 1) return RKL_EINVAL;
-  if (coeff_flags & RKL_FLUX_FORM) return RKL_EINVAL;  // full rows do not fit the static layout
+  if (coeff_flags & (RKL_FLUX_FORM | RKL_ACROSS_POLE)) return RKL_EINVAL;  // not in the static layout
   if (!device_resident(T) || !device_resident(bhat) || !device_resident(n) || !device_resident(u))
     return RKL_EINVAL;  // no host staging here: that would need device buffers
   cudaStream_t stream = (cudaStream_t)cuda_stream;

@@ -199,6 +199,11 @@ __global__ void __launch_bounds__(RB) k_assemble_A(Dims d, const double *__restr
     for (int s = 0; s < NS; s++)
       acoef[s * d.N + c] = s == DIAG ? fma(dt, coef[s * d.N + c], W[c]) : dt * coef[s * d.N + c];
   }
+  if (OP == OPK_POLE) {  // the across-pole entries after the slots
+    const long long np = pole_extra(d), o = (long long)NS * d.N;
+    for (long long e = (long long)blockIdx.x * RB + threadIdx.x; e < np; e += (long long)gridDim.x * RB)
+      acoef[o + e] = dt * coef[o + e];
+  }
 }
 
 // y = A p with A from k_assemble_A ; alpha = r.z / p.y
@@ -436,18 +441,39 @@ __global__ void __launch_bounds__(RB) k_pupdate_jacobi(long long N, const T *__r
     p[c] = fma(b, p[c], r[c] * dinv[c]);
 }
 
+// x += alpha p ; r -= alpha y ; r.r for the convergence test of the block-ILU0 solve that
+// follows (this kernel is bound by memory, so its FP64 product is free; FP32 fields sum the
+// products of four cells in FP32 before the FP64 accumulation)
 template <typename T>
 __global__ void __launch_bounds__(RB) k_xr_update(long long N, T *__restrict__ x,
                                                   const T *__restrict__ p,
                                                   T *__restrict__ r,
                                                   const T *__restrict__ y,
-                                                  const PcgState *st) {
+                                                  double *partials, unsigned int *counter,
+                                                  PcgState *st) {
   if (st->status != PCG_RUNNING) return;
   const T a = (T)st->alpha;
+  double v[1] = {0.0};
+  T part = T(0);
+  int cnt = 0;
   for (long long c = (long long)blockIdx.x * RB + threadIdx.x; c < N; c += (long long)gridDim.x * RB) {
     x[c] = fma(a, p[c], x[c]);
-    r[c] = fma(-a, y[c], r[c]);
+    const T rv = fma(-a, y[c], r[c]);
+    r[c] = rv;
+    if constexpr (std::is_same<T, float>::value) {
+      part = fmaf(rv, rv, part);
+      if (++cnt == 4) {
+        v[0] += (double)part;
+        part = 0.f;
+        cnt = 0;
+      }
+    } else {
+      v[0] = fma(rv, rv, v[0]);
+    }
   }
+  v[0] += (double)part;
+  double tot[1];
+  if (grid_sum<1, RB>(v, partials, counter, tot) && threadIdx.x == 0) st->rnorm2 = tot[0];
 }
 
 template <typename T>
@@ -474,7 +500,10 @@ __global__ void __launch_bounds__(RB) k_scale_to_f32(long long N, const double *
     v[0] = fma((double)rv, (double)rv, v[0]);
   }
   double tot[1];
-  if (grid_sum<1, RB>(v, partials, counter, tot) && threadIdx.x == 0) st->bnorm2 = tot[0];
+  if (grid_sum<1, RB>(v, partials, counter, tot) && threadIdx.x == 0) {
+    st->bnorm2 = tot[0];
+    st->rnorm2 = tot[0];  // e = 0: the inner residual is the right-hand side
+  }
 }
 
 // x += sigma e (FP64)
@@ -529,10 +558,12 @@ __device__ __forceinline__ int slot_of_offset(int di, int dj, int dk) {
   return -1;
 }
 
+template <int OP> constexpr int ilu_pat() { return OP == OPK_VISC ? 7 : 19; }
+
 // position inside a group's [G * bs] slot array of block bb's local cell l
 __device__ __forceinline__ int group_pos(const IluPlan &pl, int bb, int l) {
   int li = l % pl.bi, lj = (l / pl.bi) % pl.bj, lk = l / (pl.bi * pl.bj);
-  int lev = li + 2 * lj + 3 * lk;
+  int lev = ilu_level(pl.pat, li, lj, lk);
   int ls = pl.lev_start[lev], nl = pl.lev_start[lev + 1] - ls;
   return pl.G * ls + bb * nl + (pl.pos_of[l] - ls);
 }
@@ -544,10 +575,11 @@ __global__ void __launch_bounds__(GB) k_bilu_factor(Dims d, IluPlan pl,
                                                     const double *__restrict__ coef,
                                                     const double *__restrict__ W, double dt,
                                                     double *__restrict__ LU) {
+  constexpr int PAT = ilu_pat<OP>();
   const int grp = blockIdx.x, b0 = grp * pl.G;
   const int gcount = min(pl.G, pl.nblocks - b0);
   const size_t gs = (size_t)pl.G * pl.bs;
-  double *LUg = LU + (size_t)grp * ILU_SLOTS * gs;
+  double *LUg = LU + (size_t)grp * ilu_nslots(PAT) * gs;
   const int nf = OP == RKL_OP_VISCOSITY ? 3 : 9;
   for (int lev = 0; lev < pl.nlev; lev++) {
     const int ls = pl.lev_start[lev], nl = pl.lev_start[lev + 1] - ls;
@@ -573,20 +605,19 @@ __global__ void __launch_bounds__(GB) k_bilu_factor(Dims d, IluPlan pl,
           if (lex_rank(q2) == rk) s = q2;
         if (s < 0 || !in_pattern<OP>(pl, b, s)) continue;
         const int kp = group_pos(pl, bb, l + slot_ldelta(pl, s));
-        const double L = a[s] / LUg[kp];
+        const double L = a[s] / LUg[kp];  // U_kk, slot 0
         a[s] = L;
         for (int q2 = 0; q2 < NSL; q2++) {
           if (lex_rank(q2) <= rk || !in_pattern<OP>(pl, b, q2)) continue;
           int s3 = slot_of_offset(slot_di(q2) - slot_di(s), slot_dj(q2) - slot_dj(s),
                                   slot_dk(q2) - slot_dk(s));
-          if (s3 < 0) continue;
-          if (OP == RKL_OP_VISCOSITY && s3 != 0 && (((s3 - 1) % 9) >= 3)) continue;
-          a[q2] -= L * LUg[(size_t)s3 * gs + kp];
+          if (s3 < 0 || lu_slot(PAT, s3) < 0) continue;
+          a[q2] -= L * LUg[(size_t)lu_slot(PAT, s3) * gs + kp];
         }
       }
       for (int q2 = 0; q2 < NSL; q2++)
-        LUg[(size_t)q2 * gs + p] = in_pattern<OP>(pl, b, q2) ? a[q2] : 0.0;
-      LUg[(size_t)(ILU_SLOTS - 1) * gs + p] = 1.0 / a[0];
+        if (lu_slot(PAT, q2) >= 0) LUg[(size_t)lu_slot(PAT, q2) * gs + p] = in_pattern<OP>(pl, b, q2) ? a[q2] : 0.0;
+      LUg[(size_t)lu_slot(PAT, 19) * gs + p] = 1.0 / a[0];
     }
     __syncthreads();
   }
@@ -600,8 +631,9 @@ __global__ void __launch_bounds__(GB) k_bilu_factor(Dims d, IluPlan pl,
 // pattern mask, offset in the grid) is tabulated once per CTA in shared memory.
 constexpr int AB = 384;
 // the solve depends only on the pattern kept by the factorisation: the flux form keeps
-// the 19-point pattern of symmetric conduction
-constexpr int ilu_op(int op) { return op == OPK_FLUX ? OPK_COND : op; }
+// the 19-point pattern of symmetric conduction, and so does the across-pole form (its
+// couplings to the antipodal column leave every block)
+constexpr int ilu_op(int op) { return op == OPK_FLUX || op == OPK_POLE ? OPK_COND : op; }
 constexpr int ILU_TAB_BYTES = (8192 + 64) * 8 + 4096 * 4 * 2 + 64 * 8;  // zs + tab + goff + base
 // per-block stride of the staged residual: odd, so that the same local cell of the G
 // blocks of a group falls into different shared-memory banks
@@ -615,6 +647,9 @@ __global__ void __launch_bounds__(AB) k_bilu_apply(Dims d, IluPlan pl,
                                                    unsigned int *counter, PcgState *st,
                                                    int init) {
   if (!init && st->status != PCG_RUNNING) return;
+  constexpr int PAT = ilu_pat<OP>();
+  constexpr int NF = PAT == 7 ? 3 : 9;  // lower (and upper) couplings of a row
+  constexpr int SU = lu_slot(PAT, 10), SINV = lu_slot(PAT, 19);
   extern __shared__ double smem[];
   const int bs = pl.bs;
   const int zst = ilu_zstride(bs);
@@ -625,7 +660,7 @@ __global__ void __launch_bounds__(AB) k_bilu_apply(Dims d, IluPlan pl,
   const int grp = blockIdx.x, b0 = grp * pl.G;
   const int gcount = min(pl.G, pl.nblocks - b0);
   const size_t gs = (size_t)pl.G * bs;
-  const T *LUg = LU + (size_t)grp * ILU_SLOTS * gs;
+  const T *LUg = LU + (size_t)grp * ilu_nslots(PAT) * gs;
   const int tid = threadIdx.x;
 
   for (int pp = tid; pp < bs; pp += AB) {
@@ -634,10 +669,12 @@ __global__ void __launch_bounds__(AB) k_bilu_apply(Dims d, IluPlan pl,
     b.li = l % pl.bi;
     b.lj = (l / pl.bi) % pl.bj;
     b.lk = l / (pl.bi * pl.bj);
-    int mask = 0;
+    int mask = 0;  // bit m: lower coupling m, bit 9 + m: upper coupling m
 #pragma unroll
-    for (int s = 1; s < NSL; s++)
-      if (in_pattern<OP>(pl, b, s)) mask |= 1 << (s - 1);
+    for (int m = 0; m < NF; m++) {
+      if (in_pattern<OP>(pl, b, 1 + m)) mask |= 1 << m;
+      if (in_pattern<OP>(pl, b, 10 + m)) mask |= 1 << (9 + m);
+    }
     tab[pp] = l | (mask << 12);
     goff[l] = (int)(b.li + (long long)d.nr * b.lj + d.nrt * b.lk);
   }
@@ -651,31 +688,31 @@ __global__ void __launch_bounds__(AB) k_bilu_apply(Dims d, IluPlan pl,
     const int bb = q / bs;
     zs[bb * zst + (q - bb * bs)] = r[base[bb] + goff[q - bb * bs]];
   }
-  int dl[NSL];  // local-index offset of every slot
+  int dl[NF];  // local-index offset of lower coupling m (of upper coupling m: -dl[m])
 #pragma unroll
-  for (int s = 0; s < NSL; s++) dl[s] = slot_ldelta(pl, s);
+  for (int m = 0; m < NF; m++) dl[m] = slot_ldelta(pl, 1 + m);
 
   // ---- forward sweep: z* = r - L z* ----
-  T pre[9];
+  T pre[NF];
   {
     const int nl = pl.lev_start[1] - pl.lev_start[0];
     if (tid < gcount * nl) {
 #pragma unroll
-      for (int s = 1; s < 10; s++) pre[s - 1] = LUg[(size_t)s * gs + tid];
+      for (int m = 0; m < NF; m++) pre[m] = LUg[(size_t)(1 + m) * gs + tid];
     }
   }
   __syncthreads();
   for (int lev = 0; lev < pl.nlev; lev++) {
     const int ls = pl.lev_start[lev], nl = pl.lev_start[lev + 1] - ls;
-    T cur[9];
+    T cur[NF];
 #pragma unroll
-    for (int s = 0; s < 9; s++) cur[s] = pre[s];
+    for (int m = 0; m < NF; m++) cur[m] = pre[m];
     if (lev + 1 < pl.nlev) {
       const int ls2 = pl.lev_start[lev + 1], nl2 = pl.lev_start[lev + 2] - ls2;
       if (tid < gcount * nl2) {
         const size_t p2 = (size_t)pl.G * ls2 + tid;
 #pragma unroll
-        for (int s = 1; s < 10; s++) pre[s - 1] = LUg[(size_t)s * gs + p2];
+        for (int m = 0; m < NF; m++) pre[m] = LUg[(size_t)(1 + m) * gs + p2];
       }
     }
     for (int q = tid; q < gcount * nl; q += AB) {
@@ -685,13 +722,13 @@ __global__ void __launch_bounds__(AB) k_bilu_apply(Dims d, IluPlan pl,
       T v = zb[l];
       if (q == tid) {
 #pragma unroll
-        for (int s = 1; s < 10; s++)
-          if (mask & (1 << (s - 1))) v = fma(-cur[s - 1], zb[l + dl[s]], v);
+        for (int m = 0; m < NF; m++)
+          if (mask & (1 << m)) v = fma(-cur[m], zb[l + dl[m]], v);
       } else {
         const size_t p = (size_t)pl.G * ls + q;
 #pragma unroll
-        for (int s = 1; s < 10; s++)
-          if (mask & (1 << (s - 1))) v = fma(-LUg[(size_t)s * gs + p], zb[l + dl[s]], v);
+        for (int m = 0; m < NF; m++)
+          if (mask & (1 << m)) v = fma(-LUg[(size_t)(1 + m) * gs + p], zb[l + dl[m]], v);
       }
       zb[l] = v;
     }
@@ -699,26 +736,28 @@ __global__ void __launch_bounds__(AB) k_bilu_apply(Dims d, IluPlan pl,
   }
 
   // ---- backward sweep: z = (z* - U z) / U_ii ----
-  T preb[10];
+  T preb[NF + 1];
   {
     const int lsl = pl.lev_start[pl.nlev - 1], nl = pl.lev_start[pl.nlev] - lsl;
     if (tid < gcount * nl) {
       const size_t p = (size_t)pl.G * lsl + tid;
 #pragma unroll
-      for (int s = 10; s < ILU_SLOTS; s++) preb[s - 10] = LUg[(size_t)s * gs + p];
+      for (int m = 0; m < NF; m++) preb[m] = LUg[(size_t)(SU + m) * gs + p];
+      preb[NF] = LUg[(size_t)SINV * gs + p];
     }
   }
   for (int lev = pl.nlev - 1; lev >= 0; lev--) {
     const int ls = pl.lev_start[lev], nl = pl.lev_start[lev + 1] - ls;
-    T cur[10];
+    T cur[NF + 1];
 #pragma unroll
-    for (int s = 0; s < 10; s++) cur[s] = preb[s];
+    for (int m = 0; m <= NF; m++) cur[m] = preb[m];
     if (lev > 0) {
       const int ls2 = pl.lev_start[lev - 1], nl2 = ls - ls2;
       if (tid < gcount * nl2) {
         const size_t p2 = (size_t)pl.G * ls2 + tid;
 #pragma unroll
-        for (int s = 10; s < ILU_SLOTS; s++) preb[s - 10] = LUg[(size_t)s * gs + p2];
+        for (int m = 0; m < NF; m++) preb[m] = LUg[(size_t)(SU + m) * gs + p2];
+        preb[NF] = LUg[(size_t)SINV * gs + p2];
       }
     }
     for (int q = tid; q < gcount * nl; q += AB) {
@@ -728,24 +767,24 @@ __global__ void __launch_bounds__(AB) k_bilu_apply(Dims d, IluPlan pl,
       T v = zb[l];
       if (q == tid) {
 #pragma unroll
-        for (int s = 10; s < NSL; s++)
-          if (mask & (1 << (s - 1))) v = fma(-cur[s - 10], zb[l + dl[s]], v);
-        zb[l] = v * cur[9];
+        for (int m = 0; m < NF; m++)
+          if (mask & (1 << (9 + m))) v = fma(-cur[m], zb[l - dl[m]], v);
+        zb[l] = v * cur[NF];
       } else {
         const size_t p = (size_t)pl.G * ls + q;
 #pragma unroll
-        for (int s = 10; s < NSL; s++)
-          if (mask & (1 << (s - 1))) v = fma(-LUg[(size_t)s * gs + p], zb[l + dl[s]], v);
-        zb[l] = v * LUg[(size_t)(ILU_SLOTS - 1) * gs + p];
+        for (int m = 0; m < NF; m++)
+          if (mask & (1 << (9 + m))) v = fma(-LUg[(size_t)(SU + m) * gs + p], zb[l - dl[m]], v);
+        zb[l] = v * LUg[(size_t)SINV * gs + p];
       }
     }
     __syncthreads();
   }
-  double v2[2] = {0.0, 0.0};
-  // r.z and r.r: FP64 products per cell for the FP64 solve; for the FP32 solve the
-  // products of four successive cells of a thread are summed in FP32 before the FP64
-  // accumulation, as in the FP32 SpMV and Jacobi update
-  T prz = T(0), prr = T(0);
+  double v1[1] = {0.0};
+  // r.z (r.r comes from the x, r update before this kernel): FP64 products per cell for
+  // the FP64 solve; for the FP32 solve the products of four successive cells of a thread
+  // are summed in FP32 before the FP64 accumulation, as in the FP32 SpMV and Jacobi update
+  T prz = T(0);
   int cnt = 0;
   for (int q = tid; q < gcount * bs; q += AB) {
     const int bb = q / bs;
@@ -754,22 +793,19 @@ __global__ void __launch_bounds__(AB) k_bilu_apply(Dims d, IluPlan pl,
     z[c] = zv;
     if constexpr (std::is_same<T, float>::value) {
       prz = fmaf(rv, zv, prz);
-      prr = fmaf(rv, rv, prr);
       if (++cnt == 4) {
-        v2[0] += (double)prz;
-        v2[1] += (double)prr;
-        prz = prr = 0.f;
+        v1[0] += (double)prz;
+        prz = 0.f;
         cnt = 0;
       }
     } else {
-      v2[0] = fma(rv, zv, v2[0]);
-      v2[1] = fma(rv, rv, v2[1]);
+      v1[0] = fma(rv, zv, v1[0]);
     }
   }
-  v2[0] += (double)prz;
-  v2[1] += (double)prr;
-  double tot[2];
-  if (grid_sum<2, AB>(v2, partials, counter, tot) && threadIdx.x == 0) finalize_dots(st, tot[0], tot[1], init != 0);
+  v1[0] += (double)prz;
+  double tot[1];
+  if (grid_sum<1, AB>(v1, partials, counter, tot) && threadIdx.x == 0)
+    finalize_dots(st, tot[0], st->rnorm2, init != 0);
 }
 
 unsigned int march_grid(const rkl_ctx *ctx, int op) {
@@ -807,23 +843,27 @@ int march_setup_spmv(rkl_ctx *ctx) {
 // shape, dt or the operator changed since the last factorisation.
 int bilu0_prepare(rkl_ctx *ctx, const int *block, double dt) {
   const Dims &d = ctx->d;
+  const int pat = ctx->op == OPK_VISC ? 7 : 19;  // pattern kept by the zero-fill ILU
   if (ctx->lu_valid && ctx->lu_blk[0] == block[0] && ctx->lu_blk[1] == block[1] &&
-      ctx->lu_blk[2] == block[2] && ctx->lu_dt == dt)
+      ctx->lu_blk[2] == block[2] && ctx->lu_dt == dt && ctx->plan.pat == pat)
     return RKL_OK;
   int bi = block[0], bj = block[1], bk = block[2], bs = bi * bj * bk;
-  if (ctx->plan.bs != bs || ctx->plan.bi != bi || ctx->plan.bj != bj || ctx->plan.bk != bk) {
-    int nlev = (bi - 1) + 2 * (bj - 1) + 3 * (bk - 1) + 1;
+  if (ctx->plan.bs != bs || ctx->plan.bi != bi || ctx->plan.bj != bj || ctx->plan.bk != bk ||
+      ctx->plan.pat != pat) {
+    // wavefronts l = li + 2 lj + 3 lk (19-point: every lower neighbour, (1,-1,0) included,
+    // has a smaller l) or l = li + lj + lk (7-point); lexicographic order within a wavefront
+    const int nlev = ilu_level(pat, bi - 1, bj - 1, bk - 1) + 1;
     std::vector<int> start(nlev + 1, 0), cell(bs), pos(bs);
     for (int lk = 0; lk < bk; lk++)
       for (int lj = 0; lj < bj; lj++)
-        for (int li = 0; li < bi; li++) start[li + 2 * lj + 3 * lk + 1]++;
+        for (int li = 0; li < bi; li++) start[ilu_level(pat, li, lj, lk) + 1]++;
     for (int l = 0; l < nlev; l++) start[l + 1] += start[l];
     std::vector<int> fill(start.begin(), start.end() - 1);
     for (int lk = 0; lk < bk; lk++)
       for (int lj = 0; lj < bj; lj++)
         for (int li = 0; li < bi; li++) {
           int l = li + bi * (lj + bj * lk);
-          int p = fill[li + 2 * lj + 3 * lk]++;
+          int p = fill[ilu_level(pat, li, lj, lk)]++;
           cell[p] = l;
           pos[l] = p;
         }
@@ -846,7 +886,7 @@ int bilu0_prepare(rkl_ctx *ctx, const int *block, double dt) {
     rc = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "upload ILU plan");
     if (rc) return rc;
     IluPlan &pl = ctx->plan;
-    pl.bi = bi; pl.bj = bj; pl.bk = bk; pl.bs = bs; pl.nlev = nlev;
+    pl.bi = bi; pl.bj = bj; pl.bk = bk; pl.bs = bs; pl.nlev = nlev; pl.pat = pat;
     pl.nbi = d.nr / bi; pl.nbj = d.nth / bj; pl.nbk = d.nph / bk;
     pl.nblocks = pl.nbi * pl.nbj * pl.nbk;
     // G blocks per CTA: enough rows per wavefront to fill the warps but at most AB rows
@@ -877,7 +917,7 @@ int bilu0_prepare(rkl_ctx *ctx, const int *block, double dt) {
                       "ILU shared memory");
     if (rc) return rc;
   }
-  const size_t need = (size_t)ILU_SLOTS * ctx->plan.ngroups * ctx->plan.G * ctx->plan.bs;
+  const size_t need = (size_t)ilu_nslots(pat) * ctx->plan.ngroups * ctx->plan.G * ctx->plan.bs;
   int rc;
   if (need > ctx->lu_cap) {
     if (ctx->LU) {
@@ -1038,7 +1078,8 @@ static void queue_chunk(rkl_ctx *ctx, const PcgFields<T> &f, double dt, int pc, 
     } else {
       {
         ProfScope prof(ctx, RKL_K_PCG_UPDATE, q);
-        k_xr_update<T><<<L.g, RB, 0, ctx->stream>>>(N, f.x, f.p, f.r, f.y, ctx->d_state);
+        k_xr_update<T><<<L.g, RB, 0, ctx->stream>>>(N, f.x, f.p, f.r, f.y, ctx->partials, ctx->counter,
+                                                    ctx->d_state);
       }
       {
         ProfScope prof(ctx, RKL_K_BILU_APPLY, q);
@@ -1190,7 +1231,8 @@ static int pcg_run(rkl_ctx *ctx, double *x, const double *u, const double *x0, d
     cudaFree(ctx->acoef);
     ctx->acoef = nullptr;
     ctx->acoef_slots = 0;
-    if ((rc = cuda_check(ctx, cudaMalloc(&ctx->acoef, op_ncoef(OP) * N * sizeof(double)), "alloc A")))
+    if ((rc = cuda_check(ctx, cudaMalloc(&ctx->acoef, (op_ncoef(OP) * N + pole_extra(d)) * sizeof(double)),
+                         "alloc A")))
       return rc;
     ctx->acoef_slots = op_ncoef(OP);
   }

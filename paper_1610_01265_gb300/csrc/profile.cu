@@ -95,7 +95,10 @@ constexpr int PEAK_THREADS = 256;
 
 // PEAK_CHAINS independent a <- a * b + c chains per thread (b < 1: every chain converges to
 // c / (1 - b), so the values stay finite); the sums are stored so that no chain is dead code.
-__global__ void __launch_bounds__(PEAK_THREADS) k_dfma_peak(int iters, double b, double c, double *out) {
+// b and c are moved into registers first (an FMA whose operands come from the constant
+// bank does not issue at the full FP64 rate).
+__global__ void __launch_bounds__(PEAK_THREADS) k_dfma_peak(int iters, double b_in, double c_in, double *out) {
+  const double b = __shfl_sync(0xffffffffu, b_in, 0), c = __shfl_sync(0xffffffffu, c_in, 0);
   double a[PEAK_CHAINS];
 #pragma unroll
   for (int q = 0; q < PEAK_CHAINS; q++) a[q] = 1e-3 * threadIdx.x + q;

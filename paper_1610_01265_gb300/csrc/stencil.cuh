@@ -101,11 +101,36 @@ __device__ __forceinline__ T S_apply_full(const Dims &d, const T *__restrict__ c
   return acc;
 }
 
+// Symmetric 19-point conduction with across-pole theta-ghosts: the stored symmetric part
+// plus, in the two pole rows (nth >= 2), the five couplings to the antipodal column kept
+// at coef + 10 N (internal.cuh).  Other rows are exactly S_apply_cond.
+template <typename T>
+__device__ __forceinline__ T S_apply_pole(const Dims &d, const T *__restrict__ coef,
+                                          const T *__restrict__ u, long long c, const Nbr &n) {
+  T acc = S_apply_cond<T>(d, coef, u, c, n);
+  if (n.vtm && n.vtp) return acc;
+  const long long q = c / d.nr;
+  const int i = (int)(c - q * d.nr), k = (int)(q / d.nth);
+  const int side = n.vtm ? 1 : 0;  // j = 0 has no theta-minus neighbour
+  const T *P = coef + 10 * d.N;
+  const long long stride = 2LL * d.nph * d.nr, e = ((long long)side * d.nph + k) * d.nr + i;
+  const int h = d.nph / 2;
+  const int kb = k + h < d.nph ? k + h : k + h - d.nph;
+  const long long cb = c + (long long)(kb - k) * d.nrt;  // the antipodal cell (same i, j)
+  acc = fma(P[e], u[cb], acc);
+  if (i < d.nr - 1) acc = fma(P[stride + e], u[cb + 1], acc);
+  if (i > 0) acc = fma(P[2 * stride + e], u[cb - 1], acc);
+  acc = fma(P[3 * stride + e], u[cb + (kb < d.nph - 1 ? d.nrt : -(long long)(d.nph - 1) * d.nrt)], acc);
+  acc = fma(P[4 * stride + e], u[cb + (kb > 0 ? -d.nrt : (long long)(d.nph - 1) * d.nrt)], acc);
+  return acc;
+}
+
 template <int OP, typename T>
 __device__ __forceinline__ T S_apply(const Dims &d, const T *__restrict__ coef,
                                      const T *__restrict__ u, long long c, const Nbr &n) {
   if (OP == RKL_OP_CONDUCTION) return S_apply_cond<T>(d, coef, u, c, n);
   if (OP == OPK_FLUX) return S_apply_full<T>(d, coef, u, c, n);
+  if (OP == OPK_POLE) return S_apply_pole<T>(d, coef, u, c, n);
   return S_apply_visc<T>(d, coef, u, c, n);
 }
 

@@ -32,6 +32,7 @@ RKL_F64 = 0
 RKL_F32MIX = 1
 RKL_BETA_TCUT = 1
 RKL_FLUX_FORM = 2
+RKL_ACROSS_POLE = 4
 RKL_FORCE_ODD = 1
 
 EXPORTED = ("rkl_create", "rkl_destroy", "rkl_set_stream", "rkl_strerror", "rkl_last_error",
@@ -258,8 +259,9 @@ class Context:
         return dt.value
 
     def set_conduction(self, T, bhat, n, kappa0: float = 9e-7, beta_tcut: bool = False,
-                       flux_form: bool = False) -> float:
-        flags = (RKL_BETA_TCUT if beta_tcut else 0) | (RKL_FLUX_FORM if flux_form else 0)
+                       flux_form: bool = False, across_pole: bool = False) -> float:
+        flags = ((RKL_BETA_TCUT if beta_tcut else 0) | (RKL_FLUX_FORM if flux_form else 0)
+                 | (RKL_ACROSS_POLE if across_pole else 0))
         return self.set_coeffs(RKL_OP_CONDUCTION, T, bhat, n, kappa0, flags)
 
     def set_viscosity(self, rho, nu) -> float:
