@@ -824,7 +824,7 @@ def profile_case(args):
             for _ in range(2):
                 net.loss_grad((nr, nth, nph), feat, tgt, want_loss=False)
                 net.adam(1e-3)
-        torch.cuda.synchronize()
+        net.check()
         net.close()
         print(f"profile case {args.profile} done")
         return 0
@@ -1173,6 +1173,7 @@ def warmstart_study(seed=1, dims=GRID, n_steps=WS_STEPS, n_train=WS_TRAIN, ratio
         e1.record()
         torch.cuda.synchronize()
         fwd_ms.append(e0.elapsed_time(e1))
+    net.check()  # every tensor-core convolution of the study finished
     g_ms = statistics.median(fwd_ms)
     bf16_peak = measured_peaks().get("bf16_tflops", 1900.0)
     out = {

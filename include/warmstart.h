@@ -28,8 +28,8 @@
  * Memory: arguments named "device" must be CUDA device pointers; parameter and
  * gradient vectors may be host or device (copied).  Activation buffers are owned by the
  * handle and grow to the largest pass seen.  Every call is asynchronous on the handle's
- * stream except ws_create, ws_set_params, ws_get_params, ws_get_grads and ws_loss_grad
- * with loss_out != NULL, which return after the stream has drained.
+ * stream except ws_create, ws_set_params, ws_get_params, ws_get_grads, ws_check and
+ * ws_loss_grad with loss_out != NULL, which return after the stream has drained.
  * Errors: RKL_OK or a negative RKL_E* code of rklpcg.h; ws_last_error() gives the last
  * CUDA message.  A handle is not thread-safe.
  */
@@ -91,6 +91,12 @@ int ws_features(rkl_ws *ws, const rkl_grid *grid, const double *T, const double 
  * alias T.  grid->r_faces is not used. */
 int ws_guess(rkl_ws *ws, const rkl_grid *grid, const double *T, const double *bhat,
              double dt, double scale, double *x0);
+
+/* Drain the handle's stream and report whether every tensor-core convolution since the
+ * last check finished: RKL_ECUDA (message in ws_last_error, flag cleared) if one gave up
+ * waiting for its MMAs after about two seconds, in which case the outputs of the calls
+ * since the last check are not valid.  ws_loss_grad with loss_out != NULL checks too. */
+int ws_check(rkl_ws *ws);
 
 /* Training target of one solve: target[i] = (x[i] - base[i]) / unit in FP32 for n cells
  * (x, base device float64, target device float32), e.g. x = the PCG solution and

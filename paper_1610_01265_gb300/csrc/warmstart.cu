@@ -282,6 +282,229 @@ __global__ void __launch_bounds__(CONV_THREADS, 2) k_conv(ConvArgs a) {
   }
 }
 
+// ---- tcgen05 implicit-GEMM convolution: CIN in {16, 32} -> 32 channels, grids with nr a
+// multiple of 128 ----
+//
+// A work unit is one column of TC_T = 2 theta rows x 128 r cells of one box, over a chunk of
+// TC_CHUNK phi planes, marched plane by plane.  Each staged plane holds the 4 theta lines
+// (the two rows and their halo) x 130 r cells (with the r halo) of the input, channels-last
+// BF16, in the no-swizzle K-major layout of the tensor-core descriptors: for every 8-channel
+// slab, one 16-byte row per cell, rows contiguous.  The A operand of a tap is then a window
+// of 128 consecutive rows of one staged plane (the tap's shift is an offset of the start
+// address), M = 128 cells; B is the tap's 32 x CIN weight block, resident in shared memory;
+// N = 32, K = 16 per instruction, FP32 accumulators in tensor memory (TMEM).  One thread
+// issues the 27 x CIN/16 MMAs of each of the plane's two tiles and commits them to an
+// mbarrier; TMEM holds two planes of accumulators, so the MMAs of plane k run while the
+// epilogue of plane k - 1 (TMEM -> registers, bias + ReLU or the ReLU mask, BF16) stores it.
+// A ring of five staged planes lets plane k + 2 load (cp.async) while plane k computes.
+constexpr int TC_R = 128, TC_T = 2, TC_LINES = TC_T + 2, TC_ROWS = TC_R + 2, TC_PROWS = TC_LINES * TC_ROWS;
+constexpr int TC_RING = 5, TC_THREADS = 256, TC_CHUNK = 32, TC_TMEM_COLS = 128;
+constexpr long long TC_WAIT = 4000000000LL;  // ~2 s at the maximum SM clock
+
+template <int CIN> constexpr int tc_wbytes() { return NTAP * (CIN / 8) * 32 * 16; }
+template <int CIN> constexpr int tc_plane_bytes() { return (CIN / 8) * TC_PROWS * 16; }
+template <int CIN> constexpr int tc_smem_bytes() { return tc_wbytes<CIN>() + TC_RING * tc_plane_bytes<CIN>() + 256; }
+
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+// kind::f16 instruction descriptor: FP32 accumulate, BF16 A and B, both K-major, M = 128, N = 32
+constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | (4u << 17) | (8u << 24);
+
+// D[tmem] (+)= A B^T, M = 128, N = 32, K = 16, BF16 in, FP32 accumulate
+__device__ __forceinline__ void umma_bf16(uint32_t d, uint64_t ad, uint64_t bd, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+      "l"(ad), "l"(bd), "r"(TC_IDESC), "r"(acc));
+}
+
+__device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t parity) {
+  const long long t0 = clock64();
+  uint32_t ok = 0;
+  while (!ok) {
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+    if (!ok && clock64() - t0 > TC_WAIT) return false;
+  }
+  return true;
+}
+
+struct TcArgs {
+  Boxes g;
+  const __nv_bfloat16 *in;    // [cells][CIN]
+  const __nv_bfloat16 *wum;   // [27][CIN / 8][32][8] weight blocks (rows = output channel)
+  const float *bias;          // [32] (EPI_RELU) or NULL
+  const __nv_bfloat16 *mask;  // [cells][32] (EPI_MASK)
+  __nv_bfloat16 *out;         // [cells][32]
+  long long nunits;
+  int nchunk;                 // phi chunks per column
+  int *kerr;                  // set when a bounded wait runs out
+};
+
+template <int CIN, int EPI>
+__global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
+  constexpr int NS = CIN / 8, PB = tc_plane_bytes<CIN>(), SLAB = TC_PROWS * 16;
+  extern __shared__ __align__(128) unsigned char smem[];
+  unsigned char *wsm = smem;                        // weights
+  unsigned char *ring = smem + tc_wbytes<CIN>();    // TC_RING staged planes
+  float *bias_s = reinterpret_cast<float *>(ring + TC_RING * PB);
+  uint64_t *bar = reinterpret_cast<uint64_t *>(bias_s + 32);  // [2]
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 2);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t wsm_u = smem_u32(wsm), ring_u = smem_u32(ring);
+
+  for (int q = tid; q < tc_wbytes<CIN>() / 16; q += TC_THREADS)
+    cp_async16(wsm + q * 16, reinterpret_cast<const unsigned char *>(a.wum) + q * 16, 16);
+  if (tid < 32) bias_s[tid] = (EPI == EPI_RELU && a.bias) ? a.bias[tid] : 0.0f;
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[1])));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(TC_TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+  uint32_t nbatch = 0;  // MMA batches committed so far (buffer nbatch & 1)
+  bool ok = true;
+
+  // stage plane k (absolute phi index) of the column into ring slot s
+  auto stage = [&](const BrickPos &p, int k, int s) {
+    unsigned char *dst = ring + s * PB;
+    for (int q = tid; q < TC_PROWS * NS; q += TC_THREADS) {
+      const int row = q / NS, c = q - row * NS;
+      const int line = row / TC_ROWS, rr = row - line * TC_ROWS;
+      const long long cell = cell_index(a.g, p.b, p.i0 + rr - 1, p.j0 + line - 1, k);
+      const __nv_bfloat16 *gp = cell >= 0 ? a.in + cell * CIN + c * 8 : a.in;
+      cp_async16(dst + c * SLAB + row * 16, gp, cell >= 0 ? 16 : 0);
+    }
+    asm volatile("cp.async.commit_group;\n" ::);
+  };
+  // epilogue of the plane whose accumulators are in buffer `buf`
+  auto epilogue = [&](const BrickPos &p, int k, uint32_t buf) {
+    const int t = warp >> 2, q4 = warp & 3, m = 32 * q4 + lane;
+    const uint32_t taddr = tmem + ((uint32_t)(32 * q4) << 16) + buf * 64 + t * 32;
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    const int i = p.i0 + m, j = p.j0 + t;
+    if (i >= a.g.nr || j >= a.g.nth || k >= a.g.nph) return;
+    const long long cell = (long long)p.b * a.g.nc + ((long long)k * a.g.nth + j) * a.g.nr + i;
+    __align__(16) __nv_bfloat16 o[32];
+    if (EPI == EPI_RELU) {
+#pragma unroll
+      for (int c = 0; c < 32; c++) o[c] = __float2bfloat16_rn(fmaxf(__uint_as_float(r[c]) + bias_s[c], 0.0f));
+    } else {
+      __align__(16) __nv_bfloat16 mk[32];
+      const uint4 *ms = reinterpret_cast<const uint4 *>(a.mask + cell * 32);
+#pragma unroll
+      for (int v = 0; v < 4; v++) reinterpret_cast<uint4 *>(mk)[v] = ms[v];
+#pragma unroll
+      for (int c = 0; c < 32; c++)
+        o[c] = __float2bfloat16_rn(__bfloat162float(mk[c]) > 0.0f ? __uint_as_float(r[c]) : 0.0f);
+    }
+    uint4 *dst = reinterpret_cast<uint4 *>(a.out + cell * 32);
+#pragma unroll
+    for (int v = 0; v < 4; v++) dst[v] = reinterpret_cast<const uint4 *>(o)[v];
+  };
+
+  for (long long u = blockIdx.x; u < a.nunits; u += gridDim.x) {
+    // unit -> (box, r segment, theta pair, phi chunk)
+    long long rest = u;
+    const int ch = (int)(rest % a.nchunk);
+    rest /= a.nchunk;
+    const int nseg = a.g.nr / TC_R, npair = (a.g.nth + TC_T - 1) / TC_T;
+    const int seg = (int)(rest % nseg);
+    rest /= nseg;
+    const int pair = (int)(rest % npair);
+    BrickPos p;
+    p.b = (int)(rest / npair);
+    p.i0 = seg * TC_R;
+    p.j0 = pair * TC_T;
+    const int k0 = ch * TC_CHUNK, k1 = min(a.g.nph, k0 + TC_CHUNK);
+    p.k0 = k0;
+    // ring slot of plane k: (k - k0 + 1) mod TC_RING
+    auto slot = [&](int k) { return (k - k0 + 1 + TC_RING) % TC_RING; };
+    stage(p, k0 - 1, slot(k0 - 1));
+    stage(p, k0, slot(k0));
+    stage(p, k0 + 1, slot(k0 + 1));
+    for (int k = k0; k < k1; k++) {
+      stage(p, k + 2, slot(k + 2));  // its slot held plane k - 3, last read by the MMAs of plane k - 2
+      asm volatile("cp.async.wait_group 1;\n" ::: "memory");  // planes up to k + 1 have landed
+      __syncthreads();
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
+      const uint32_t buf = nbatch & 1;
+      if (tid == 0 && ok) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // descriptors of the three staged planes a tap reads and of the weights; a tap's
+        // operand is a constant offset from them (shared addresses stay below 2^18 bytes, so
+        // adding offset >> 4 to the 14-bit start field never carries into the next field)
+        uint64_t ad0[3];
+#pragma unroll
+        for (int dp = 0; dp < 3; dp++) ad0[dp] = umma_desc(ring_u + slot(k + dp - 1) * PB, SLAB, 128);
+        const uint64_t bd0 = umma_desc(wsm_u, 512, 128);
+#pragma unroll
+        for (int t = 0; t < TC_T; t++) {
+          const uint32_t d = tmem + buf * 64 + t * 32;
+#pragma unroll
+          for (int tap = 0; tap < NTAP; tap++) {
+            const int dr = tap % 3 - 1, dt = (tap / 3) % 3 - 1, dp = tap / 9;
+            const uint32_t arow = (uint32_t)((t + 1 + dt) * TC_ROWS + 1 + dr);
+#pragma unroll
+            for (int ks = 0; ks < CIN / 16; ks++) {
+              const uint64_t ad = ad0[dp] + ((arow * 16 + 2 * ks * SLAB) >> 4);
+              const uint64_t bd = bd0 + (((tap * NS + 2 * ks) * 512) >> 4);
+              umma_bf16(d, ad, bd, (tap > 0 || ks > 0) ? 1u : 0u);
+            }
+          }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(&bar[buf]))
+                     : "memory");
+      }
+      nbatch++;
+      if (k > k0) {  // epilogue of plane k - 1 while the MMAs of plane k run
+        const uint32_t pb = (nbatch - 2) & 1, par = ((nbatch - 2) >> 1) & 1;
+        if (ok && !tc_wait(smem_u32(&bar[pb]), par)) ok = false;
+        ok = __syncthreads_and(ok);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (ok) epilogue(p, k - 1, pb);
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      }
+      __syncthreads();
+    }
+    {  // epilogue of the chunk's last plane
+      const uint32_t pb = (nbatch - 1) & 1, par = ((nbatch - 1) >> 1) & 1;
+      if (ok && !tc_wait(smem_u32(&bar[pb]), par)) ok = false;
+      ok = __syncthreads_and(ok);
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (ok) epilogue(p, k1 - 1, pb);
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");  // the last prefetched planes
+    __syncthreads();
+  }
+  if (!ok && tid == 0) atomicOr(a.kerr, 1);
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS));
+}
+
 struct WgArgs {
   Boxes g;
   const __nv_bfloat16 *in;    // [cells][CIN] layer input activation
@@ -436,6 +659,28 @@ __global__ void k_wfrag(const __nv_bfloat16 *__restrict__ w, int cin, int cout, 
   out[idx] = make_uint2(pack(2 * q), pack(2 * q + 8));
 }
 
+// B blocks of the tcgen05 convolution, [tap][cin / 8][32][8] (row n = output channel of the
+// convolution, 8 consecutive input channels): forward B[n][k] = W[n][k][tap]; adjoint
+// B[n][k] = W[k][n][26 - tap].  Channels beyond the layer's real counts are zero.
+__global__ void k_wumma(const __nv_bfloat16 *__restrict__ w, int cin, int cout, int CIN, int adjoint,
+                        __nv_bfloat16 *__restrict__ out) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= NTAP * CIN * 32) return;
+  const int e = idx % 8, n = (idx / 8) % 32, slab = (idx / 256) % (CIN / 8), tap = idx / (256 * (CIN / 8));
+  const int k = slab * 8 + e;
+  int co, ci, t;
+  if (!adjoint) {
+    co = n;
+    ci = k;
+    t = tap;
+  } else {
+    co = k;
+    ci = n;
+    t = NTAP - 1 - tap;
+  }
+  out[idx] = (co < cout && ci < cin) ? w[((size_t)co * cin + ci) * NTAP + t] : __float2bfloat16(0.0f);
+}
+
 __global__ void __launch_bounds__(EW) k_to_bf16(int n, const float *__restrict__ a, __nv_bfloat16 *__restrict__ b) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q < n) b[q] = __float2bfloat16_rn(a[q]);
@@ -572,6 +817,9 @@ struct rkl_ws {
   __nv_bfloat16 *wbf = nullptr;
   uint2 *wfrag[NL] = {nullptr, nullptr, nullptr, nullptr};  // forward fragments
   uint2 *wadj[NL] = {nullptr, nullptr, nullptr, nullptr};   // adjoint fragments (layers 1..3)
+  __nv_bfloat16 *wum[NL] = {nullptr, nullptr, nullptr, nullptr};   // tcgen05 weight blocks (layers 0..2)
+  __nv_bfloat16 *wuma[NL] = {nullptr, nullptr, nullptr, nullptr};  // tcgen05 adjoint blocks (layers 1..3)
+  int *kerr = nullptr;  // set by a tcgen05 convolution whose bounded wait ran out
   long long step = 0;
   unsigned char *arena = nullptr;
   size_t arena_cap = 0;
@@ -596,6 +844,8 @@ int ws_cuda(rkl_ws *ws, cudaError_t e) {
 }
 
 int frag_ks(int l) { return L_CIN[l] <= 16 ? 1 : 2; }
+// channels of a tcgen05 convolution input (K padded to a multiple of 16)
+int tc_cin(int c) { return c <= 16 ? 16 : 32; }
 int frag_nt(int l) { return L_COUT[l] == 1 ? 1 : 4; }
 size_t frag_count(int l) { return (size_t)NTAP * frag_ks(l) * frag_nt(l) * 32; }
 // adjoint of layer l (l >= 1): input = gradient at its output (16 channels for l = 3)
@@ -615,6 +865,10 @@ int configure_kernels(rkl_ws *ws) {
   if (!rc) rc = set_smem(ws, k_wgrad<16, 32>, wgrad_smem_bytes<16, 32>());
   if (!rc) rc = set_smem(ws, k_wgrad<32, 32>, wgrad_smem_bytes<32, 32>());
   if (!rc) rc = set_smem(ws, k_wgrad<32, 16>, wgrad_smem_bytes<32, 16>());
+  if (!rc) rc = set_smem(ws, k_conv_tc<16, EPI_RELU>, tc_smem_bytes<16>());
+  if (!rc) rc = set_smem(ws, k_conv_tc<32, EPI_RELU>, tc_smem_bytes<32>());
+  if (!rc) rc = set_smem(ws, k_conv_tc<16, EPI_MASK>, tc_smem_bytes<16>());
+  if (!rc) rc = set_smem(ws, k_conv_tc<32, EPI_MASK>, tc_smem_bytes<32>());
   return rc;
 }
 
@@ -631,6 +885,18 @@ int refresh_weights(rkl_ws *ws) {
       const int na = (int)adj_count(l);
       k_wfrag<<<(na + EW - 1) / EW, EW, 0, ws->stream>>>(ws->wbf + ws->bw_off[l], L_CIN[l], L_COUT[l],
                                                         L_COUT[l] == 1 ? 1 : 2, 4, 1, ws->wadj[l]);
+      ws->launches += 1;
+    }
+    if (l < NL - 1) {  // tcgen05 forward blocks: input channels padded to 16 or 32
+      const int CIN = tc_cin(L_CIN[l]), n = NTAP * CIN * 32;
+      k_wumma<<<(n + EW - 1) / EW, EW, 0, ws->stream>>>(ws->wbf + ws->bw_off[l], L_CIN[l], L_COUT[l], CIN, 0,
+                                                       ws->wum[l]);
+      ws->launches += 1;
+    }
+    if (l > 0) {  // tcgen05 adjoint blocks: the adjoint's input is the gradient at the output
+      const int CIN = tc_cin(L_COUT[l]), n = NTAP * CIN * 32;
+      k_wumma<<<(n + EW - 1) / EW, EW, 0, ws->stream>>>(ws->wbf + ws->bw_off[l], L_CIN[l], L_COUT[l], CIN, 1,
+                                                       ws->wuma[l]);
       ws->launches += 1;
     }
   }
@@ -661,6 +927,28 @@ int ensure_part(rkl_ws *ws, size_t floats) {
   int rc = ws_cuda(ws, cudaMalloc(&ws->part, floats * sizeof(float)));
   if (!rc) ws->part_cap = floats;
   return rc;
+}
+
+// the tcgen05 convolution takes 16- or 32-channel inputs, 32 outputs, and grids whose r
+// extent is a multiple of 128 (one UMMA tile per r line)
+bool tc_applies(const Boxes &g) { return g.nr % TC_R == 0; }
+
+template <int CIN, int EPI>
+void launch_conv_tc(rkl_ws *ws, const Boxes &g, const __nv_bfloat16 *in, const __nv_bfloat16 *wum, const float *bias,
+                    const __nv_bfloat16 *mask, __nv_bfloat16 *out) {
+  TcArgs a;
+  a.g = g;
+  a.in = in;
+  a.wum = wum;
+  a.bias = bias;
+  a.mask = mask;
+  a.out = out;
+  a.nchunk = (g.nph + TC_CHUNK - 1) / TC_CHUNK;
+  a.nunits = (long long)g.nbox * (g.nr / TC_R) * ((g.nth + TC_T - 1) / TC_T) * a.nchunk;
+  a.kerr = ws->kerr;
+  const long long grid = a.nunits < ws->nsm ? a.nunits : ws->nsm;
+  k_conv_tc<CIN, EPI><<<(unsigned)grid, TC_THREADS, tc_smem_bytes<CIN>(), ws->stream>>>(a);
+  ws->launches += 1;
 }
 
 int conv_grid(const rkl_ws *ws, const Boxes &g) {
@@ -728,9 +1016,15 @@ int carve(rkl_ws *ws, long long cells, bool training, Bufs &b) {
 }
 
 void run_forward(rkl_ws *ws, const Boxes &g, const Bufs &b) {
-  launch_conv<16, 4, EPI_RELU>(ws, g, b.a0, ws->wfrag[0], ws->param + ws->boff[0], nullptr, b.a1);
-  launch_conv<32, 4, EPI_RELU>(ws, g, b.a1, ws->wfrag[1], ws->param + ws->boff[1], nullptr, b.a2);
-  launch_conv<32, 4, EPI_RELU>(ws, g, b.a2, ws->wfrag[2], ws->param + ws->boff[2], nullptr, b.a3);
+  if (tc_applies(g)) {
+    launch_conv_tc<16, EPI_RELU>(ws, g, b.a0, ws->wum[0], ws->param + ws->boff[0], nullptr, b.a1);
+    launch_conv_tc<32, EPI_RELU>(ws, g, b.a1, ws->wum[1], ws->param + ws->boff[1], nullptr, b.a2);
+    launch_conv_tc<32, EPI_RELU>(ws, g, b.a2, ws->wum[2], ws->param + ws->boff[2], nullptr, b.a3);
+  } else {
+    launch_conv<16, 4, EPI_RELU>(ws, g, b.a0, ws->wfrag[0], ws->param + ws->boff[0], nullptr, b.a1);
+    launch_conv<32, 4, EPI_RELU>(ws, g, b.a1, ws->wfrag[1], ws->param + ws->boff[1], nullptr, b.a2);
+    launch_conv<32, 4, EPI_RELU>(ws, g, b.a2, ws->wfrag[2], ws->param + ws->boff[2], nullptr, b.a3);
+  }
   launch_conv<32, 1, EPI_F32>(ws, g, b.a3, ws->wfrag[3], ws->param + ws->boff[3], nullptr, b.y);
 }
 
@@ -777,7 +1071,13 @@ int ws_create(rkl_ws **out, unsigned long long seed, void *cuda_stream) {
   for (int l = 0; l < NL && !rc; l++) {
     rc = ws_cuda(ws, cudaMalloc(&ws->wfrag[l], sizeof(uint2) * frag_count(l)));
     if (!rc && l > 0) rc = ws_cuda(ws, cudaMalloc(&ws->wadj[l], sizeof(uint2) * adj_count(l)));
+    if (!rc && l < NL - 1)
+      rc = ws_cuda(ws, cudaMalloc(&ws->wum[l], sizeof(__nv_bfloat16) * NTAP * tc_cin(L_CIN[l]) * 32));
+    if (!rc && l > 0)
+      rc = ws_cuda(ws, cudaMalloc(&ws->wuma[l], sizeof(__nv_bfloat16) * NTAP * tc_cin(L_COUT[l]) * 32));
   }
+  if (!rc) rc = ws_cuda(ws, cudaMalloc(&ws->kerr, sizeof(int)));
+  if (!rc) rc = ws_cuda(ws, cudaMemset(ws->kerr, 0, sizeof(int)));
   if (!rc) rc = configure_kernels(ws);
   if (!rc) {
     std::vector<float> p(ws->nparam, 0.0f);
@@ -807,7 +1107,10 @@ int ws_destroy(rkl_ws *ws) {
   for (int l = 0; l < NL; l++) {
     if (ws->wfrag[l]) cudaFree(ws->wfrag[l]);
     if (ws->wadj[l]) cudaFree(ws->wadj[l]);
+    if (ws->wum[l]) cudaFree(ws->wum[l]);
+    if (ws->wuma[l]) cudaFree(ws->wuma[l]);
   }
+  if (ws->kerr) cudaFree(ws->kerr);
   cudaGetLastError();
   delete ws;
   return RKL_OK;
@@ -886,13 +1189,16 @@ int ws_loss_grad(rkl_ws *ws, const int box[3], int nbox, int periodic_phi, const
   ws->launches += 3;
   // layer 4: dW4 from (dy, a3); dz3 = W4^T dy masked by a3 > 0
   if ((rc = launch_wgrad<32, 16>(ws, g, b.a3, b.dy, 3))) return rc;
-  launch_conv<16, 4, EPI_MASK>(ws, g, b.dy, ws->wadj[3], nullptr, b.a3, b.dzA);
+  if (tc_applies(g)) launch_conv_tc<16, EPI_MASK>(ws, g, b.dy, ws->wuma[3], nullptr, b.a3, b.dzA);
+  else launch_conv<16, 4, EPI_MASK>(ws, g, b.dy, ws->wadj[3], nullptr, b.a3, b.dzA);
   // layer 3: dW3 from (dz3, a2); dz2 = W3^T dz3 masked by a2 > 0
   if ((rc = launch_wgrad<32, 32>(ws, g, b.a2, b.dzA, 2))) return rc;
-  launch_conv<32, 4, EPI_MASK>(ws, g, b.dzA, ws->wadj[2], nullptr, b.a2, b.dzB);
+  if (tc_applies(g)) launch_conv_tc<32, EPI_MASK>(ws, g, b.dzA, ws->wuma[2], nullptr, b.a2, b.dzB);
+  else launch_conv<32, 4, EPI_MASK>(ws, g, b.dzA, ws->wadj[2], nullptr, b.a2, b.dzB);
   // layer 2: dW2 from (dz2, a1); dz1 = W2^T dz2 masked by a1 > 0
   if ((rc = launch_wgrad<32, 32>(ws, g, b.a1, b.dzB, 1))) return rc;
-  launch_conv<32, 4, EPI_MASK>(ws, g, b.dzB, ws->wadj[1], nullptr, b.a1, b.dzA);
+  if (tc_applies(g)) launch_conv_tc<32, EPI_MASK>(ws, g, b.dzB, ws->wuma[1], nullptr, b.a1, b.dzA);
+  else launch_conv<32, 4, EPI_MASK>(ws, g, b.dzB, ws->wadj[1], nullptr, b.a1, b.dzA);
   // layer 1: dW1 from (dz1, a0)
   if ((rc = launch_wgrad<16, 32>(ws, g, b.a0, b.dzA, 0))) return rc;
   if ((rc = ws_cuda(ws, cudaGetLastError()))) return rc;
@@ -900,7 +1206,7 @@ int ws_loss_grad(rkl_ws *ws, const int box[3], int nbox, int periodic_phi, const
     std::vector<double> h(2 * RED_BLOCKS);
     rc = ws_cuda(ws, cudaMemcpyAsync(h.data(), ws->red, sizeof(double) * 2 * RED_BLOCKS, cudaMemcpyDeviceToHost,
                                      ws->stream));
-    if (!rc) rc = ws_cuda(ws, cudaStreamSynchronize(ws->stream));
+    if (!rc) rc = ws_check(ws);
     if (rc) return rc;
     double wsum = 0.0, l = 0.0;
     for (int q = 0; q < RED_BLOCKS; q++) wsum += h[q];
@@ -954,6 +1260,21 @@ int ws_guess(rkl_ws *ws, const rkl_grid *grid, const double *T, const double *bh
   k_guess<<<eg, EW, 0, ws->stream>>>(N, T, b.y, scale, x0);
   ws->launches += 2;
   return ws_cuda(ws, cudaGetLastError());
+}
+
+int ws_check(rkl_ws *ws) {
+  if (!ws) return RKL_EINVAL;
+  int flag = 0;
+  int rc = ws_cuda(ws, cudaMemcpyAsync(&flag, ws->kerr, sizeof(int), cudaMemcpyDeviceToHost, ws->stream));
+  if (!rc) rc = ws_cuda(ws, cudaStreamSynchronize(ws->stream));
+  if (rc) return rc;
+  if (flag) {
+    snprintf(ws->err, sizeof(ws->err), "%s",
+             "a tensor-core convolution gave up waiting for its MMAs; its outputs are not valid");
+    rc = ws_cuda(ws, cudaMemsetAsync(ws->kerr, 0, sizeof(int), ws->stream));
+    return rc ? rc : RKL_ECUDA;
+  }
+  return RKL_OK;
 }
 
 int ws_target(rkl_ws *ws, long long n, const double *x, const double *base, double unit, float *target) {

@@ -15,7 +15,7 @@ from . import rklpcg as R
 
 EXPORTED = ("ws_num_params", "ws_create", "ws_destroy", "ws_set_stream", "ws_last_error",
             "ws_kernel_launches", "ws_set_params", "ws_get_params", "ws_get_grads", "ws_set_grads",
-            "ws_forward", "ws_loss_grad", "ws_adam", "ws_features", "ws_guess", "ws_target")
+            "ws_forward", "ws_loss_grad", "ws_adam", "ws_features", "ws_guess", "ws_target", "ws_check")
 LAYERS = ((5, 32), (32, 32), (32, 32), (32, 1))
 
 _bound = False
@@ -43,6 +43,7 @@ def load():
         lib.ws_features.argtypes = [P, ctypes.POINTER(R._Grid), P, P, D, P]
         lib.ws_guess.argtypes = [P, ctypes.POINTER(R._Grid), P, P, D, D, P]
         lib.ws_target.argtypes = [P, ctypes.c_longlong, P, P, D, P]
+        lib.ws_check.argtypes = [P]
         _bound = True
     return lib
 
@@ -173,3 +174,8 @@ class Net:
         n = x.numel()
         self._check(self._lib.ws_target(self._h, n, _p(x, np.float64, n), _p(base, np.float64, n), float(unit),
                                         _p(out, np.float32, n)), "ws_target")
+
+    def check(self):
+        """Drain the stream; raise if a tensor-core convolution since the last check gave up
+        waiting for its MMAs (its outputs would not be valid)."""
+        self._check(self._lib.ws_check(self._h), "ws_check")

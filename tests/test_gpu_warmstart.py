@@ -61,8 +61,13 @@ def test_initial_parameters_bitwise(env):
         net.close()
 
 
+# shapes are (nph, nth, nr); r extents that are multiples of 128 run the 32-channel layers on
+# the tcgen05 convolution (one 128-cell r line per UMMA tile: odd theta counts, a second r
+# segment whose halo comes from the first, phi chunks and wrap), the others on mma.sync
 @pytest.mark.parametrize("shape,nbox,periodic", [((10, 9, 37), 1, True), ((3, 5, 20), 3, False),
-                                                 ((2, 4, 64), 2, True), ((1, 1, 1), 1, True)])
+                                                 ((2, 4, 64), 2, True), ((1, 1, 1), 1, True),
+                                                 ((6, 5, 128), 1, True), ((3, 3, 256), 2, False),
+                                                 ((40, 2, 128), 1, True)])
 def test_forward_parity(env, shape, nbox, periodic):
     torch, OW, W = env
     params = _params(OW, 3)
@@ -73,6 +78,7 @@ def test_forward_parity(env, shape, nbox, periodic):
     y = torch.empty(f_dev[0].numel(), dtype=torch.float32, device="cuda")
     box = (shape[2], shape[1], shape[0])
     net.forward(box, f_dev.view(-1), y, nbox=nbox, periodic=periodic)
+    net.check()
     y_o, _ = OW.forward(params, OW.bf16(feats.astype(np.float32)), periodic=periodic)
     y_g = y.cpu().numpy().reshape(y_o.shape)
     assert _rel(y_g, y_o.numpy()) <= FWD_TOL
@@ -80,10 +86,11 @@ def test_forward_parity(env, shape, nbox, periodic):
     net.close()
 
 
-@pytest.mark.parametrize("periodic,weighted", [(True, False), (False, True)])
-def test_loss_gradient_parity(env, periodic, weighted):
+@pytest.mark.parametrize("periodic,weighted,shape", [(True, False, (4, 6, 40)), (False, True, (4, 6, 40)),
+                                                      (True, True, (5, 3, 128))])
+def test_loss_gradient_parity(env, periodic, weighted, shape):
     torch, OW, W = env
-    shape, nbox = (4, 6, 40), 2
+    nbox = 2
     params = _params(OW, 5)
     feats = np.stack([_feats_grid(OW, shape, 20 + b)[1] for b in range(nbox)])
     target = synth.random_field((nbox,) + shape, 31).astype(np.float32)
@@ -146,6 +153,7 @@ def test_features_and_guess_parity(env):
     x0 = torch.empty_like(T)
     scale = 2.5e3
     net.guess(shape, T, b, dt, scale, x0)
+    net.check()
     y_o, _ = OW.forward(params, OW.features(c["T"], c["bhat"], dt), periodic=True)
     x_o = c["T"] + scale * y_o[0].numpy()
     dx = x0.cpu().numpy().reshape(shape) - c["T"]
@@ -186,6 +194,7 @@ def test_fullsize_guess_sampled(env):
     x0 = torch.empty_like(T)
     dt, scale = 55.0, 1e4
     net.guess((nph, nth, nr), T, b, dt, scale, x0)
+    net.check()
     x = x0.cpu().numpy().reshape(nph, nth, nr)
     feats = OW.features(c["T"], c["bhat"], dt)
     rng = np.random.default_rng(3)
