@@ -25,11 +25,13 @@
 // W'[ci][co][26 - tap] = W[co][ci][tap].  Weight gradient: per tap, M = Cout, N = Cin,
 // K = cells, both operands through ldmatrix.trans; a persistent CTA accumulates its
 // bricks in registers and a second kernel sums the per-CTA partials in FP64.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
 #include <cstdio>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -289,21 +291,32 @@ __global__ void __launch_bounds__(CONV_THREADS, 2) k_conv(ConvArgs a) {
 // TC_CHUNK phi planes, marched plane by plane.  Each staged plane holds the 4 theta lines
 // (the two rows and their halo) x 130 r cells (with the r halo) of the input, channels-last
 // BF16, in the no-swizzle K-major layout of the tensor-core descriptors: for every 8-channel
-// slab, one 16-byte row per cell, rows contiguous.  The A operand of a tap is then a window
-// of 128 consecutive rows of one staged plane (the tap's shift is an offset of the start
-// address), M = 128 cells; B is the tap's 32 x CIN weight block, resident in shared memory;
-// N = 32, K = 16 per instruction, FP32 accumulators in tensor memory (TMEM).  One thread
-// issues the 27 x CIN/16 MMAs of each of the plane's two tiles and commits them to an
-// mbarrier; TMEM holds two planes of accumulators, so the MMAs of plane k run while the
-// epilogue of plane k - 1 (TMEM -> registers, bias + ReLU or the ReLU mask, BF16) stores it.
-// A ring of five staged planes lets plane k + 2 load (cp.async) while plane k computes.
+// slab, one 16-byte row per cell, rows contiguous ([slab][line][130 cells][8 channels]).  One
+// 5-D TMA copy brings a plane in (zero fill outside the box in r and theta).  The A operand
+// of a tap is a window of 128 consecutive rows of one staged plane (the tap's shift is an
+// offset of the start address), M = 128 cells; B is the tap's 32 x CIN weight block,
+// resident in shared memory; N = 32, K = 16 per instruction, FP32 accumulators in tensor
+// memory (TMEM).
+//
+// The CTA is warp-specialised and its roles meet only at mbarriers:
+//   warp 0     loads planes into a ring of TC_RING slots (full[s] / empty[s]);
+//   warp 1     one thread issues the 2 tiles x 27 taps x CIN/16 MMAs of a plane into one of
+//              two TMEM accumulator buffers (tfull[b] / tempty[b]) and, by a commit, frees
+//              the slot of the plane that no later MMA reads;
+//   warp 2     allocates and frees the TMEM columns;
+//   warps 4-7  epilogue: TMEM -> registers (warp w reads TMEM lanes 32 (w mod 4) ..), bias +
+//              ReLU or the ReLU mask of the adjoint, BF16 stores.
+// Every wait is bounded; one that runs out raises a shared abort flag that ends all roles,
+// the kernel error word is set, and the CTA waits (bounded) for its copies and MMAs in
+// flight before it frees TMEM and returns.
 constexpr int TC_R = 128, TC_T = 2, TC_LINES = TC_T + 2, TC_ROWS = TC_R + 2, TC_PROWS = TC_LINES * TC_ROWS;
 constexpr int TC_RING = 5, TC_THREADS = 256, TC_CHUNK = 32, TC_TMEM_COLS = 128;
 constexpr long long TC_WAIT = 4000000000LL;  // ~2 s at the maximum SM clock
 
 template <int CIN> constexpr int tc_wbytes() { return NTAP * (CIN / 8) * 32 * 16; }
 template <int CIN> constexpr int tc_plane_bytes() { return (CIN / 8) * TC_PROWS * 16; }
-template <int CIN> constexpr int tc_smem_bytes() { return tc_wbytes<CIN>() + TC_RING * tc_plane_bytes<CIN>() + 256; }
+// weights, ring, 128 bytes of alignment slack, bias + barriers + TMEM slot + abort flag
+template <int CIN> constexpr int tc_smem_bytes() { return tc_wbytes<CIN>() + TC_RING * tc_plane_bytes<CIN>() + 384; }
 
 __device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
   return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
@@ -319,21 +332,61 @@ __device__ __forceinline__ void umma_bf16(uint32_t d, uint64_t ad, uint64_t bd, 
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
       "l"(ad), "l"(bd), "r"(TC_IDESC), "r"(acc));
 }
-
-__device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t parity) {
+// arrive on `bar` once every tcgen05 operation this thread has issued so far has completed
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tc_bar_init(uint64_t *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void tc_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void tc_expect_tx(uint64_t *bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool tc_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// wait for the phase of `parity`; false when another role has aborted, or after TC_WAIT
+// cycles (which raises the abort flag)
+__device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t parity, volatile int *abort_s) {
   const long long t0 = clock64();
-  uint32_t ok = 0;
-  while (!ok) {
-    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-                 : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
-    if (!ok && clock64() - t0 > TC_WAIT) return false;
+  while (!tc_try_wait(bar, parity)) {
+    if (*abort_s) return false;
+    if (clock64() - t0 > TC_WAIT) {
+      *abort_s = 1;
+      return false;
+    }
   }
   return true;
+}
+// teardown wait: ignores the abort flag, still bounded
+__device__ __forceinline__ void tc_drain(uint64_t *bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!tc_try_wait(bar, parity) && clock64() - t0 <= TC_WAIT) {
+  }
+}
+// 5-D tiled TMA load of one box into shared memory, completing on `bar`
+__device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+                                            int c4, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, "
+      "%6}], [%7];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(bar))
+      : "memory");
 }
 
 struct TcArgs {
   Boxes g;
-  const __nv_bfloat16 *in;    // [cells][CIN]
   const __nv_bfloat16 *wum;   // [27][CIN / 8][32][8] weight blocks (rows = output channel)
   const float *bias;          // [32] (EPI_RELU) or NULL
   const __nv_bfloat16 *mask;  // [cells][32] (EPI_MASK)
@@ -343,166 +396,241 @@ struct TcArgs {
   int *kerr;                  // set when a bounded wait runs out
 };
 
+struct TcUnit {
+  int b, i0, j0, k0, k1;
+};
+// unit -> (box, theta pair, r segment, phi chunk), the chunk fastest
+__device__ __forceinline__ TcUnit tc_unit(const TcArgs &a, long long u) {
+  TcUnit p;
+  const int ch = (int)(u % a.nchunk);
+  u /= a.nchunk;
+  const int nseg = a.g.nr / TC_R, npair = (a.g.nth + TC_T - 1) / TC_T;
+  const int seg = (int)(u % nseg);
+  u /= nseg;
+  const int pair = (int)(u % npair);
+  p.b = (int)(u / npair);
+  p.i0 = seg * TC_R;
+  p.j0 = pair * TC_T;
+  p.k0 = ch * TC_CHUNK;
+  p.k1 = min(a.g.nph, p.k0 + TC_CHUNK);
+  return p;
+}
+
+// in: the tensor map of the [cells][CIN] input, dims {8 channels, r, theta, CIN / 8 slabs,
+// box * phi}, box {8, 130, 4, CIN / 8, 1}
 template <int CIN, int EPI>
-__global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
+__global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(const __grid_constant__ CUtensorMap in, TcArgs a) {
   constexpr int NS = CIN / 8, PB = tc_plane_bytes<CIN>(), SLAB = TC_PROWS * 16;
-  extern __shared__ __align__(128) unsigned char smem[];
-  unsigned char *wsm = smem;                        // weights
-  unsigned char *ring = smem + tc_wbytes<CIN>();    // TC_RING staged planes
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+  unsigned char *wsm = smem;                      // weights
+  unsigned char *ring = smem + tc_wbytes<CIN>();  // TC_RING staged planes
   float *bias_s = reinterpret_cast<float *>(ring + TC_RING * PB);
-  uint64_t *bar = reinterpret_cast<uint64_t *>(bias_s + 32);  // [2]
-  uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 2);
+  uint64_t *full = reinterpret_cast<uint64_t *>(bias_s + 32);
+  uint64_t *empty = full + TC_RING;
+  uint64_t *tfull = empty + TC_RING;
+  uint64_t *tempty = tfull + 2;
+  uint64_t *done = tempty + 2;
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(done + 1);
+  volatile int *abort_s = reinterpret_cast<volatile int *>(tslot + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t wsm_u = smem_u32(wsm), ring_u = smem_u32(ring);
+  const int nph = a.g.nph;
 
   for (int q = tid; q < tc_wbytes<CIN>() / 16; q += TC_THREADS)
     cp_async16(wsm + q * 16, reinterpret_cast<const unsigned char *>(a.wum) + q * 16, 16);
   if (tid < 32) bias_s[tid] = (EPI == EPI_RELU && a.bias) ? a.bias[tid] : 0.0f;
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[0])));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[1])));
+    for (int s = 0; s < TC_RING; s++) {
+      tc_bar_init(&full[s], 1);
+      tc_bar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; b++) {
+      tc_bar_init(&tfull[b], 1);
+      tc_bar_init(&tempty[b], 4);
+    }
+    tc_bar_init(done, 1);
+    *abort_s = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) {
+  if (warp == 2) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
                  "r"(TC_TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   cp_async_wait_all();
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // weights, for the tensor cores
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tslot;
-  uint32_t nbatch = 0;  // MMA batches committed so far (buffer nbatch & 1)
-  bool ok = true;
 
-  // stage plane k (absolute phi index) of the column into ring slot s
-  auto stage = [&](const BrickPos &p, int k, int s) {
-    unsigned char *dst = ring + s * PB;
-    for (int q = tid; q < TC_PROWS * NS; q += TC_THREADS) {
-      const int row = q / NS, c = q - row * NS;
-      const int line = row / TC_ROWS, rr = row - line * TC_ROWS;
-      const long long cell = cell_index(a.g, p.b, p.i0 + rr - 1, p.j0 + line - 1, k);
-      const __nv_bfloat16 *gp = cell >= 0 ? a.in + cell * CIN + c * 8 : a.in;
-      cp_async16(dst + c * SLAB + row * 16, gp, cell >= 0 ? 16 : 0);
+  if (warp == 0) {
+    // ---- producer: planes k0 - 1 .. k1 of each unit, fill f into slot f mod TC_RING ----
+    long long f = 0;
+    bool ok = true;
+    for (long long u = blockIdx.x; u < a.nunits && ok; u += gridDim.x) {
+      const TcUnit p = tc_unit(a, u);
+      for (int k = p.k0 - 1; k <= p.k1; k++, f++) {
+        const int s = (int)(f % TC_RING);
+        bool w = true;
+        if (lane == 0) w = tc_wait(&empty[s], (uint32_t)((f / TC_RING) & 1) ^ 1u, abort_s);
+        if (!__shfl_sync(0xffffffffu, w, 0)) {
+          ok = false;
+          break;
+        }
+        int kk = k;
+        bool zero = false;
+        if (kk < 0 || kk >= nph) {
+          if (a.g.periodic) kk = ((kk % nph) + nph) % nph;
+          else zero = true;
+        }
+        unsigned char *dst = ring + s * PB;
+        if (!zero) {
+          if (lane == 0) {
+            tc_expect_tx(&full[s], PB);
+            tma_load_5d(dst, &in, 0, p.i0 - 1, p.j0 - 1, 0, p.b * nph + kk, &full[s]);
+          }
+        } else {  // outside a non-periodic box: zeros, written by the warp
+          for (int q = lane; q < PB / 16; q += 32) reinterpret_cast<uint4 *>(dst)[q] = make_uint4(0, 0, 0, 0);
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) tc_arrive(&full[s]);
+        }
+      }
     }
-    asm volatile("cp.async.commit_group;\n" ::);
-  };
-  // epilogue of the plane whose accumulators are in buffer `buf`
-  auto epilogue = [&](const BrickPos &p, int k, uint32_t buf) {
-    const int t = warp >> 2, q4 = warp & 3, m = 32 * q4 + lane;
-    const uint32_t taddr = tmem + ((uint32_t)(32 * q4) << 16) + buf * 64 + t * 32;
-    uint32_t r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-    const int i = p.i0 + m, j = p.j0 + t;
-    if (i >= a.g.nr || j >= a.g.nth || k >= a.g.nph) return;
-    const long long cell = (long long)p.b * a.g.nc + ((long long)k * a.g.nth + j) * a.g.nr + i;
-    __align__(16) __nv_bfloat16 o[32];
-    if (EPI == EPI_RELU) {
+    // teardown: the copies still in flight (the last fill of each slot) land before exit
+    if (lane == 0)
+      for (long long fi = f - 1; fi >= 0 && fi >= f - TC_RING; fi--)
+        tc_drain(&full[fi % TC_RING], (uint32_t)((fi / TC_RING) & 1));
+  } else if (warp == 1) {
+    // ---- MMA issuer ----
+    if (lane == 0) {
+      long long f = 0, gstep = 0;  // fill of the unit's plane k0 - 1; planes issued
+      bool ok = true;
+      for (long long u = blockIdx.x; u < a.nunits && ok; u += gridDim.x) {
+        const TcUnit p = tc_unit(a, u);
+        const int nk = p.k1 - p.k0;
+        for (int s = 0; s < nk; s++, gstep++) {
+          // planes k - 1, k, k + 1 are fills f + s .. f + s + 2
+          const int lo = s == 0 ? 0 : 2;
+          for (int e = lo; e < 3 && ok; e++)
+            ok = tc_wait(&full[(f + s + e) % TC_RING], (uint32_t)(((f + s + e) / TC_RING) & 1), abort_s);
+          const uint32_t buf = (uint32_t)(gstep & 1);
+          if (ok) ok = tc_wait(&tempty[buf], (uint32_t)((gstep >> 1) & 1) ^ 1u, abort_s);
+          if (!ok) break;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          // descriptors of the three planes a tap reads and of the weights; a tap's operand is
+          // a constant offset from them (shared addresses stay below 2^18 bytes, so adding
+          // offset >> 4 to the 14-bit start field never carries into the next field)
+          uint64_t ad0[3];
 #pragma unroll
-      for (int c = 0; c < 32; c++) o[c] = __float2bfloat16_rn(fmaxf(__uint_as_float(r[c]) + bias_s[c], 0.0f));
-    } else {
-      __align__(16) __nv_bfloat16 mk[32];
-      const uint4 *ms = reinterpret_cast<const uint4 *>(a.mask + cell * 32);
+          for (int dp = 0; dp < 3; dp++)
+            ad0[dp] = umma_desc(ring_u + (uint32_t)((f + s + dp) % TC_RING) * PB, SLAB, 128);
+          const uint64_t bd0 = umma_desc(wsm_u, 512, 128);
 #pragma unroll
-      for (int v = 0; v < 4; v++) reinterpret_cast<uint4 *>(mk)[v] = ms[v];
+          for (int t = 0; t < TC_T; t++) {
+            const uint32_t d = tmem + buf * 64 + t * 32;
 #pragma unroll
-      for (int c = 0; c < 32; c++)
-        o[c] = __float2bfloat16_rn(__bfloat162float(mk[c]) > 0.0f ? __uint_as_float(r[c]) : 0.0f);
-    }
-    uint4 *dst = reinterpret_cast<uint4 *>(a.out + cell * 32);
+            for (int tap = 0; tap < NTAP; tap++) {
+              const int dr = tap % 3 - 1, dt = (tap / 3) % 3 - 1, dp = tap / 9;
+              const uint32_t arow = (uint32_t)((t + 1 + dt) * TC_ROWS + 1 + dr);
 #pragma unroll
-    for (int v = 0; v < 4; v++) dst[v] = reinterpret_cast<const uint4 *>(o)[v];
-  };
-
-  for (long long u = blockIdx.x; u < a.nunits; u += gridDim.x) {
-    // unit -> (box, r segment, theta pair, phi chunk)
-    long long rest = u;
-    const int ch = (int)(rest % a.nchunk);
-    rest /= a.nchunk;
-    const int nseg = a.g.nr / TC_R, npair = (a.g.nth + TC_T - 1) / TC_T;
-    const int seg = (int)(rest % nseg);
-    rest /= nseg;
-    const int pair = (int)(rest % npair);
-    BrickPos p;
-    p.b = (int)(rest / npair);
-    p.i0 = seg * TC_R;
-    p.j0 = pair * TC_T;
-    const int k0 = ch * TC_CHUNK, k1 = min(a.g.nph, k0 + TC_CHUNK);
-    p.k0 = k0;
-    // ring slot of plane k: (k - k0 + 1) mod TC_RING
-    auto slot = [&](int k) { return (k - k0 + 1 + TC_RING) % TC_RING; };
-    stage(p, k0 - 1, slot(k0 - 1));
-    stage(p, k0, slot(k0));
-    stage(p, k0 + 1, slot(k0 + 1));
-    for (int k = k0; k < k1; k++) {
-      stage(p, k + 2, slot(k + 2));  // its slot held plane k - 3, last read by the MMAs of plane k - 2
-      asm volatile("cp.async.wait_group 1;\n" ::: "memory");  // planes up to k + 1 have landed
-      __syncthreads();
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncthreads();
-      const uint32_t buf = nbatch & 1;
-      if (tid == 0 && ok) {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // descriptors of the three staged planes a tap reads and of the weights; a tap's
-        // operand is a constant offset from them (shared addresses stay below 2^18 bytes, so
-        // adding offset >> 4 to the 14-bit start field never carries into the next field)
-        uint64_t ad0[3];
-#pragma unroll
-        for (int dp = 0; dp < 3; dp++) ad0[dp] = umma_desc(ring_u + slot(k + dp - 1) * PB, SLAB, 128);
-        const uint64_t bd0 = umma_desc(wsm_u, 512, 128);
-#pragma unroll
-        for (int t = 0; t < TC_T; t++) {
-          const uint32_t d = tmem + buf * 64 + t * 32;
-#pragma unroll
-          for (int tap = 0; tap < NTAP; tap++) {
-            const int dr = tap % 3 - 1, dt = (tap / 3) % 3 - 1, dp = tap / 9;
-            const uint32_t arow = (uint32_t)((t + 1 + dt) * TC_ROWS + 1 + dr);
-#pragma unroll
-            for (int ks = 0; ks < CIN / 16; ks++) {
-              const uint64_t ad = ad0[dp] + ((arow * 16 + 2 * ks * SLAB) >> 4);
-              const uint64_t bd = bd0 + (((tap * NS + 2 * ks) * 512) >> 4);
-              umma_bf16(d, ad, bd, (tap > 0 || ks > 0) ? 1u : 0u);
+              for (int ks = 0; ks < CIN / 16; ks++) {
+                const uint64_t ad = ad0[dp] + ((arow * 16 + 2 * ks * SLAB) >> 4);
+                const uint64_t bd = bd0 + (((tap * NS + 2 * ks) * 512) >> 4);
+                umma_bf16(d, ad, bd, (tap > 0 || ks > 0) ? 1u : 0u);
+              }
             }
           }
+          umma_commit(&tfull[buf]);
+          umma_commit(&empty[(f + s) % TC_RING]);  // plane k - 1: no later MMA of the unit reads it
         }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         smem_u32(&bar[buf]))
-                     : "memory");
+        if (!ok) break;
+        umma_commit(&empty[(f + nk) % TC_RING]);  // the unit's last two planes
+        umma_commit(&empty[(f + nk + 1) % TC_RING]);
+        f += nk + 2;
       }
-      nbatch++;
-      if (k > k0) {  // epilogue of plane k - 1 while the MMAs of plane k run
-        const uint32_t pb = (nbatch - 2) & 1, par = ((nbatch - 2) >> 1) & 1;
-        if (ok && !tc_wait(smem_u32(&bar[pb]), par)) ok = false;
-        ok = __syncthreads_and(ok);
+      umma_commit(done);  // teardown: every MMA issued has completed
+      tc_drain(done, 0);
+    }
+    __syncwarp();
+  } else if (warp >= 4) {
+    // ---- epilogue: plane k from TMEM buffer gstep & 1 ----
+    const int q4 = warp & 3, m = 32 * q4 + lane;
+    long long gstep = 0;
+    bool ok = true;
+    for (long long u = blockIdx.x; u < a.nunits && ok; u += gridDim.x) {
+      const TcUnit p = tc_unit(a, u);
+      for (int k = p.k0; k < p.k1; k++, gstep++) {
+        const uint32_t buf = (uint32_t)(gstep & 1);
+        long long cell[TC_T];
+#pragma unroll
+        for (int t = 0; t < TC_T; t++)
+          cell[t] = (long long)p.b * a.g.nc + ((long long)k * a.g.nth + (p.j0 + t)) * a.g.nr + p.i0 + m;
+        const bool row1 = p.j0 + 1 < a.g.nth;  // an odd theta count leaves the last pair one row
+        uint4 mk[TC_T][4];
+        if (EPI == EPI_MASK) {  // issued before the wait, so that their latency hides behind it
+#pragma unroll
+          for (int t = 0; t < TC_T; t++)
+#pragma unroll
+            for (int v = 0; v < 4; v++)
+              mk[t][v] = (t == 0 || row1) ? reinterpret_cast<const uint4 *>(a.mask + cell[t] * 32)[v]
+                                          : make_uint4(0, 0, 0, 0);
+        }
+        const bool w = tc_wait(&tfull[buf], (uint32_t)((gstep >> 1) & 1), abort_s);
+        if (!__all_sync(0xffffffffu, w)) {
+          ok = false;
+          break;
+        }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (ok) epilogue(p, k - 1, pb);
+        uint32_t r[TC_T][32];
+#pragma unroll
+        for (int t = 0; t < TC_T; t++) {
+          const uint32_t taddr = tmem + ((uint32_t)(32 * q4) << 16) + buf * 64 + t * 32;
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+              "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+              : "=r"(r[t][0]), "=r"(r[t][1]), "=r"(r[t][2]), "=r"(r[t][3]), "=r"(r[t][4]), "=r"(r[t][5]),
+                "=r"(r[t][6]), "=r"(r[t][7]), "=r"(r[t][8]), "=r"(r[t][9]), "=r"(r[t][10]), "=r"(r[t][11]),
+                "=r"(r[t][12]), "=r"(r[t][13]), "=r"(r[t][14]), "=r"(r[t][15]), "=r"(r[t][16]), "=r"(r[t][17]),
+                "=r"(r[t][18]), "=r"(r[t][19]), "=r"(r[t][20]), "=r"(r[t][21]), "=r"(r[t][22]), "=r"(r[t][23]),
+                "=r"(r[t][24]), "=r"(r[t][25]), "=r"(r[t][26]), "=r"(r[t][27]), "=r"(r[t][28]), "=r"(r[t][29]),
+                "=r"(r[t][30]), "=r"(r[t][31])
+              : "r"(taddr));
+        }
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) tc_arrive(&tempty[buf]);  // the MMAs of plane k + 2 may overwrite it
+#pragma unroll
+        for (int t = 0; t < TC_T; t++) {
+          if (t > 0 && !row1) break;
+          __align__(16) __nv_bfloat16 o[32];
+          if (EPI == EPI_RELU) {
+#pragma unroll
+            for (int c = 0; c < 32; c++)
+              o[c] = __float2bfloat16_rn(fmaxf(__uint_as_float(r[t][c]) + bias_s[c], 0.0f));
+          } else {
+            const __nv_bfloat16 *mb = reinterpret_cast<const __nv_bfloat16 *>(mk[t]);
+#pragma unroll
+            for (int c = 0; c < 32; c++)
+              o[c] = __float2bfloat16_rn(__bfloat162float(mb[c]) > 0.0f ? __uint_as_float(r[t][c]) : 0.0f);
+          }
+          uint4 *dst = reinterpret_cast<uint4 *>(a.out + cell[t] * 32);
+#pragma unroll
+          for (int v = 0; v < 4; v++) dst[v] = reinterpret_cast<const uint4 *>(o)[v];
+        }
       }
-      __syncthreads();
     }
-    {  // epilogue of the chunk's last plane
-      const uint32_t pb = (nbatch - 1) & 1, par = ((nbatch - 1) >> 1) & 1;
-      if (ok && !tc_wait(smem_u32(&bar[pb]), par)) ok = false;
-      ok = __syncthreads_and(ok);
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      if (ok) epilogue(p, k1 - 1, pb);
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    }
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");  // the last prefetched planes
-    __syncthreads();
   }
-  if (!ok && tid == 0) atomicOr(a.kerr, 1);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS));
+  if (tid == 0 && *abort_s) atomicOr(a.kerr, 1);
+  if (warp == 2) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS));
+  }
 }
 
 struct WgArgs {
@@ -933,12 +1061,49 @@ int ensure_part(rkl_ws *ws, size_t floats) {
 // extent is a multiple of 128 (one UMMA tile per r line)
 bool tc_applies(const Boxes &g) { return g.nr % TC_R == 0; }
 
+// cuTensorMapEncodeTiled, fetched once through the runtime (no link against the driver library)
+typedef CUresult (*TmapEncodeFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+TmapEncodeFn tmap_encoder() {
+  static TmapEncodeFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<TmapEncodeFn>(p);
+  });
+  return fn;
+}
+
 template <int CIN, int EPI>
-void launch_conv_tc(rkl_ws *ws, const Boxes &g, const __nv_bfloat16 *in, const __nv_bfloat16 *wum, const float *bias,
-                    const __nv_bfloat16 *mask, __nv_bfloat16 *out) {
+int launch_conv_tc(rkl_ws *ws, const Boxes &g, const __nv_bfloat16 *in, const __nv_bfloat16 *wum, const float *bias,
+                   const __nv_bfloat16 *mask, __nv_bfloat16 *out) {
+  const TmapEncodeFn enc = tmap_encoder();
+  if (!enc) {
+    snprintf(ws->err, sizeof(ws->err), "%s", "cuTensorMapEncodeTiled is not available");
+    return RKL_ECUDA;
+  }
+  // [box * phi][theta][r][CIN] viewed as {8 channels, r, theta, CIN / 8 slabs, box * phi}, so
+  // that a box lands in shared memory as [slab][line][r][8 channels]
+  CUtensorMap map;
+  const cuuint64_t dims[5] = {8, (cuuint64_t)g.nr, (cuuint64_t)g.nth, (cuuint64_t)(CIN / 8),
+                              (cuuint64_t)g.nbox * (cuuint64_t)g.nph};
+  const cuuint64_t strides[4] = {(cuuint64_t)CIN * 2, (cuuint64_t)g.nr * CIN * 2, 16,
+                                 (cuuint64_t)g.nth * g.nr * CIN * 2};
+  const cuuint32_t box[5] = {8, (cuuint32_t)TC_ROWS, (cuuint32_t)TC_LINES, (cuuint32_t)(CIN / 8), 1};
+  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  const CUresult cr = enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<__nv_bfloat16 *>(in), dims, strides,
+                          box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (cr != CUDA_SUCCESS) {
+    snprintf(ws->err, sizeof(ws->err), "cuTensorMapEncodeTiled failed (%d)", (int)cr);
+    return RKL_ECUDA;
+  }
   TcArgs a;
   a.g = g;
-  a.in = in;
   a.wum = wum;
   a.bias = bias;
   a.mask = mask;
@@ -947,8 +1112,9 @@ void launch_conv_tc(rkl_ws *ws, const Boxes &g, const __nv_bfloat16 *in, const _
   a.nunits = (long long)g.nbox * (g.nr / TC_R) * ((g.nth + TC_T - 1) / TC_T) * a.nchunk;
   a.kerr = ws->kerr;
   const long long grid = a.nunits < ws->nsm ? a.nunits : ws->nsm;
-  k_conv_tc<CIN, EPI><<<(unsigned)grid, TC_THREADS, tc_smem_bytes<CIN>(), ws->stream>>>(a);
+  k_conv_tc<CIN, EPI><<<(unsigned)grid, TC_THREADS, tc_smem_bytes<CIN>(), ws->stream>>>(map, a);
   ws->launches += 1;
+  return RKL_OK;
 }
 
 int conv_grid(const rkl_ws *ws, const Boxes &g) {
@@ -1015,17 +1181,20 @@ int carve(rkl_ws *ws, long long cells, bool training, Bufs &b) {
   return RKL_OK;
 }
 
-void run_forward(rkl_ws *ws, const Boxes &g, const Bufs &b) {
+int run_forward(rkl_ws *ws, const Boxes &g, const Bufs &b) {
+  int rc = RKL_OK;
   if (tc_applies(g)) {
-    launch_conv_tc<16, EPI_RELU>(ws, g, b.a0, ws->wum[0], ws->param + ws->boff[0], nullptr, b.a1);
-    launch_conv_tc<32, EPI_RELU>(ws, g, b.a1, ws->wum[1], ws->param + ws->boff[1], nullptr, b.a2);
-    launch_conv_tc<32, EPI_RELU>(ws, g, b.a2, ws->wum[2], ws->param + ws->boff[2], nullptr, b.a3);
+    rc = launch_conv_tc<16, EPI_RELU>(ws, g, b.a0, ws->wum[0], ws->param + ws->boff[0], nullptr, b.a1);
+    if (!rc) rc = launch_conv_tc<32, EPI_RELU>(ws, g, b.a1, ws->wum[1], ws->param + ws->boff[1], nullptr, b.a2);
+    if (!rc) rc = launch_conv_tc<32, EPI_RELU>(ws, g, b.a2, ws->wum[2], ws->param + ws->boff[2], nullptr, b.a3);
   } else {
     launch_conv<16, 4, EPI_RELU>(ws, g, b.a0, ws->wfrag[0], ws->param + ws->boff[0], nullptr, b.a1);
     launch_conv<32, 4, EPI_RELU>(ws, g, b.a1, ws->wfrag[1], ws->param + ws->boff[1], nullptr, b.a2);
     launch_conv<32, 4, EPI_RELU>(ws, g, b.a2, ws->wfrag[2], ws->param + ws->boff[2], nullptr, b.a3);
   }
+  if (rc) return rc;
   launch_conv<32, 1, EPI_F32>(ws, g, b.a3, ws->wfrag[3], ws->param + ws->boff[3], nullptr, b.y);
+  return RKL_OK;
 }
 
 bool valid_box(const int box[3], int nbox) {
@@ -1168,7 +1337,7 @@ int ws_forward(rkl_ws *ws, const int box[3], int nbox, int periodic_phi, const f
   ws->launches += 1;
   Bufs o = b;
   o.y = out;
-  run_forward(ws, g, o);
+  if ((rc = run_forward(ws, g, o))) return rc;
   return ws_cuda(ws, cudaGetLastError());
 }
 
@@ -1182,23 +1351,32 @@ int ws_loss_grad(rkl_ws *ws, const int box[3], int nbox, int periodic_phi, const
   if (rc) return rc;
   const unsigned eg = (unsigned)((cells + EW - 1) / EW);
   k_pack_input<<<eg, EW, 0, ws->stream>>>(cells, in, b.a0);
-  run_forward(ws, g, b);
+  if ((rc = run_forward(ws, g, b))) return rc;
   k_sum<<<RED_BLOCKS, EW, 0, ws->stream>>>(cells, weight, ws->red);
   k_loss<<<RED_BLOCKS, EW, 0, ws->stream>>>(cells, b.y, target, weight, ws->red, RED_BLOCKS, b.dy,
                                             ws->red + RED_BLOCKS);
   ws->launches += 3;
   // layer 4: dW4 from (dy, a3); dz3 = W4^T dy masked by a3 > 0
   if ((rc = launch_wgrad<32, 16>(ws, g, b.a3, b.dy, 3))) return rc;
-  if (tc_applies(g)) launch_conv_tc<16, EPI_MASK>(ws, g, b.dy, ws->wuma[3], nullptr, b.a3, b.dzA);
-  else launch_conv<16, 4, EPI_MASK>(ws, g, b.dy, ws->wadj[3], nullptr, b.a3, b.dzA);
+  if (tc_applies(g)) {
+    if ((rc = launch_conv_tc<16, EPI_MASK>(ws, g, b.dy, ws->wuma[3], nullptr, b.a3, b.dzA))) return rc;
+  } else {
+    launch_conv<16, 4, EPI_MASK>(ws, g, b.dy, ws->wadj[3], nullptr, b.a3, b.dzA);
+  }
   // layer 3: dW3 from (dz3, a2); dz2 = W3^T dz3 masked by a2 > 0
   if ((rc = launch_wgrad<32, 32>(ws, g, b.a2, b.dzA, 2))) return rc;
-  if (tc_applies(g)) launch_conv_tc<32, EPI_MASK>(ws, g, b.dzA, ws->wuma[2], nullptr, b.a2, b.dzB);
-  else launch_conv<32, 4, EPI_MASK>(ws, g, b.dzA, ws->wadj[2], nullptr, b.a2, b.dzB);
+  if (tc_applies(g)) {
+    if ((rc = launch_conv_tc<32, EPI_MASK>(ws, g, b.dzA, ws->wuma[2], nullptr, b.a2, b.dzB))) return rc;
+  } else {
+    launch_conv<32, 4, EPI_MASK>(ws, g, b.dzA, ws->wadj[2], nullptr, b.a2, b.dzB);
+  }
   // layer 2: dW2 from (dz2, a1); dz1 = W2^T dz2 masked by a1 > 0
   if ((rc = launch_wgrad<32, 32>(ws, g, b.a1, b.dzB, 1))) return rc;
-  if (tc_applies(g)) launch_conv_tc<32, EPI_MASK>(ws, g, b.dzB, ws->wuma[1], nullptr, b.a1, b.dzA);
-  else launch_conv<32, 4, EPI_MASK>(ws, g, b.dzB, ws->wadj[1], nullptr, b.a1, b.dzA);
+  if (tc_applies(g)) {
+    if ((rc = launch_conv_tc<32, EPI_MASK>(ws, g, b.dzB, ws->wuma[1], nullptr, b.a1, b.dzA))) return rc;
+  } else {
+    launch_conv<32, 4, EPI_MASK>(ws, g, b.dzB, ws->wadj[1], nullptr, b.a1, b.dzA);
+  }
   // layer 1: dW1 from (dz1, a0)
   if ((rc = launch_wgrad<16, 32>(ws, g, b.a0, b.dzA, 0))) return rc;
   if ((rc = ws_cuda(ws, cudaGetLastError()))) return rc;
@@ -1256,7 +1434,7 @@ int ws_guess(rkl_ws *ws, const rkl_grid *grid, const double *T, const double *bh
   if (rc) return rc;
   const unsigned eg = (unsigned)((N + EW - 1) / EW);
   k_features<<<eg, EW, 0, ws->stream>>>(N, T, bhat, (float)std::log10(dt), b.a0, nullptr);
-  run_forward(ws, g, b);
+  if ((rc = run_forward(ws, g, b))) return rc;
   k_guess<<<eg, EW, 0, ws->stream>>>(N, T, b.y, scale, x0);
   ws->launches += 2;
   return ws_cuda(ws, cudaGetLastError());
