@@ -400,11 +400,11 @@ struct TcUnit {
   int b, i0, j0, k0, k1;
 };
 // unit -> (box, theta pair, r segment, phi chunk), the chunk fastest
-__device__ __forceinline__ TcUnit tc_unit(const TcArgs &a, long long u) {
+__device__ __forceinline__ TcUnit tc_unit(const Boxes &g, int nchunk, long long u) {
   TcUnit p;
-  const int ch = (int)(u % a.nchunk);
-  u /= a.nchunk;
-  const int nseg = a.g.nr / TC_R, npair = (a.g.nth + TC_T - 1) / TC_T;
+  const int ch = (int)(u % nchunk);
+  u /= nchunk;
+  const int nseg = g.nr / TC_R, npair = (g.nth + TC_T - 1) / TC_T;
   const int seg = (int)(u % nseg);
   u /= nseg;
   const int pair = (int)(u % npair);
@@ -412,7 +412,7 @@ __device__ __forceinline__ TcUnit tc_unit(const TcArgs &a, long long u) {
   p.i0 = seg * TC_R;
   p.j0 = pair * TC_T;
   p.k0 = ch * TC_CHUNK;
-  p.k1 = min(a.g.nph, p.k0 + TC_CHUNK);
+  p.k1 = min(g.nph, p.k0 + TC_CHUNK);
   return p;
 }
 
@@ -470,7 +470,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(const __grid_constant
     long long f = 0;
     bool ok = true;
     for (long long u = blockIdx.x; u < a.nunits && ok; u += gridDim.x) {
-      const TcUnit p = tc_unit(a, u);
+      const TcUnit p = tc_unit(a.g, a.nchunk, u);
       for (int k = p.k0 - 1; k <= p.k1; k++, f++) {
         const int s = (int)(f % TC_RING);
         bool w = true;
@@ -509,7 +509,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(const __grid_constant
       long long f = 0, gstep = 0;  // fill of the unit's plane k0 - 1; planes issued
       bool ok = true;
       for (long long u = blockIdx.x; u < a.nunits && ok; u += gridDim.x) {
-        const TcUnit p = tc_unit(a, u);
+        const TcUnit p = tc_unit(a.g, a.nchunk, u);
         const int nk = p.k1 - p.k0;
         for (int s = 0; s < nk; s++, gstep++) {
           // planes k - 1, k, k + 1 are fills f + s .. f + s + 2
@@ -561,7 +561,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(const __grid_constant
     long long gstep = 0;
     bool ok = true;
     for (long long u = blockIdx.x; u < a.nunits && ok; u += gridDim.x) {
-      const TcUnit p = tc_unit(a, u);
+      const TcUnit p = tc_unit(a.g, a.nchunk, u);
       for (int k = p.k0; k < p.k1; k++, gstep++) {
         const uint32_t buf = (uint32_t)(gstep & 1);
         long long cell[TC_T];
@@ -630,6 +630,232 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(const __grid_constant
   if (warp == 2) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS));
+  }
+}
+
+// ---- output layer (32 channels -> 1) on tcgen05, grids with nr a multiple of 128 ----
+//
+// y(x) = bias + sum over taps of sum_ci a(x + d(tap))[ci] W[ci][tap].  Per staged input plane
+// the tensor cores form D[x][tap] = sum_ci a(x)[ci] W[ci][tap] for the plane's 4 lines (M = 128
+// cells, N = 32 >= 27 taps, K = 32), and y is the sum over taps of D at the tap's neighbour,
+// y(x) = bias + sum_tap D[x + d(tap)][tap]: every input is multiplied once, not once per tap.
+// Units and staging are those of k_conv_tc (one 5-D TMA copy per plane, ring of TO_RING);
+// D of the two r-halo cells of each line (outside the 128-cell tile) is formed on the CUDA
+// cores.  TMEM holds D of two planes, so the MMAs of plane k + 1 run while the sums of plane k
+// are formed: input plane k adds its contributions to the outputs of planes k - 1, k, k + 1,
+// held in registers, one output cell per thread.
+constexpr int TO_RING = 3, TO_TMEM_COLS = 256;
+constexpr int TO_DS_FLOATS = TC_LINES * NTAP * TC_ROWS;  // D of one plane, [line][tap][130 cells]
+constexpr int to_smem_bytes() { return TO_RING * tc_plane_bytes<32>() + TO_DS_FLOATS * 4 + 2048 + 384; }
+
+struct ToArgs {
+  Boxes g;
+  const __nv_bfloat16 *w;  // [32 ci][27 taps], BF16
+  const float *bias;       // [1]
+  float *y;                // [cells]
+  long long nunits;
+  int nchunk;
+  int *kerr;
+};
+
+__global__ void __launch_bounds__(TC_THREADS, 1) k_conv_out_tc(const __grid_constant__ CUtensorMap in, ToArgs a) {
+  constexpr int PB = tc_plane_bytes<32>(), SLAB = TC_PROWS * 16;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+  unsigned char *ring = smem;                                           // TO_RING staged planes
+  float *ds = reinterpret_cast<float *>(ring + TO_RING * PB);           // [4][27][130]
+  __nv_bfloat16 *wb = reinterpret_cast<__nv_bfloat16 *>(ds + TO_DS_FLOATS);  // B: [4 slabs][32 taps][8 ci]
+  uint64_t *full = reinterpret_cast<uint64_t *>(wb + 1024);             // [TO_RING]
+  uint64_t *mbar = full + TO_RING;                                      // [2] MMAs of TMEM buffer b
+  uint64_t *done = mbar + 2;
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(done + 1);
+  volatile int *abort_s = reinterpret_cast<volatile int *>(tslot + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t ring_u = smem_u32(ring), wb_u = smem_u32(wb);
+  const int nph = a.g.nph;
+
+  for (int q = tid; q < 1024; q += TC_THREADS) {
+    const int slab = q >> 8, n = (q >> 3) & 31, ci = slab * 8 + (q & 7);
+    wb[q] = n < NTAP ? a.w[ci * NTAP + n] : __float2bfloat16(0.0f);
+  }
+  if (tid == 0) {
+    for (int s = 0; s < TO_RING; s++) tc_bar_init(&full[s], 1);
+    tc_bar_init(&mbar[0], 1);
+    tc_bar_init(&mbar[1], 1);
+    tc_bar_init(done, 1);
+    *abort_s = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(TO_TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // B, for the tensor cores
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+  const float bias = a.bias[0];
+  const int t_out = tid >> 7, i_out = tid & 127;  // this thread's output cell in the tile
+  const int q4 = warp & 3, m = 32 * q4 + lane;     // TMEM lane = tile cell
+  const int L0 = (warp >> 2) * 2;                  // this warp's two lines of D
+
+  long long fill = 0, gm = 0;  // fills issued; MMA batches committed
+  long long waited = 0;        // MMA batches waited for
+  bool ok = true;
+  // stage plane kk of unit p into slot s (all threads: the zero fill of a plane outside a
+  // non-periodic box is written by the CTA)
+  auto load = [&](const TcUnit &p, int kk, int s) {
+    if (kk < 0 || kk >= nph) {
+      if (a.g.periodic) {
+        kk = ((kk % nph) + nph) % nph;
+      } else {
+        unsigned char *dst = ring + s * PB;
+        for (int q = tid; q < PB / 16; q += TC_THREADS) reinterpret_cast<uint4 *>(dst)[q] = make_uint4(0, 0, 0, 0);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) tc_arrive(&full[s]);
+        return;
+      }
+    }
+    if (tid == 0) {
+      tc_expect_tx(&full[s], PB);
+      tma_load_5d(ring + s * PB, &in, 0, p.i0 - 1, p.j0 - 1, 0, p.b * nph + kk, &full[s]);
+    }
+  };
+  // thread 0: the 8 MMAs of D for the plane of fill fi into TMEM buffer gm & 1
+  auto issue = [&](long long fi) -> bool {
+    const int s = (int)(fi % TO_RING);
+    if (!tc_wait(&full[s], (uint32_t)((fi / TO_RING) & 1), abort_s)) return false;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t buf = (uint32_t)(gm & 1);
+#pragma unroll
+    for (int L = 0; L < TC_LINES; L++)
+#pragma unroll
+      for (int ks = 0; ks < 2; ks++)
+        umma_bf16(tmem + buf * 128 + L * 32,
+                  umma_desc(ring_u + s * PB + (L * TC_ROWS + 1) * 16 + 2 * ks * SLAB, SLAB, 128),
+                  umma_desc(wb_u + 2 * ks * 512, 512, 128), ks > 0 ? 1u : 0u);
+    umma_commit(&mbar[buf]);
+    gm++;
+    return true;
+  };
+
+  for (long long u = blockIdx.x; u < a.nunits && ok; u += gridDim.x) {
+    const TcUnit p = tc_unit(a.g, a.nchunk, u);
+    const int np = p.k1 - p.k0 + 2;  // input planes k0 - 1 .. k1
+    const long long f0 = fill;
+    for (int e = 0; e < TO_RING && e < np; e++) load(p, p.k0 - 1 + e, (int)((f0 + e) % TO_RING));
+    fill = f0 + (np < TO_RING ? np : TO_RING);
+    bool ok0 = true;
+    if (tid == 0) ok0 = issue(f0);
+    if (!__syncthreads_and(ok0)) {
+      ok = false;
+      break;
+    }
+    float acc_prev = 0.0f, acc_cur = 0.0f, acc_next = 0.0f;  // outputs k - 1, k, k + 1
+    for (int e = 0; e < np; e++) {
+      const int k = p.k0 - 1 + e;
+      const int s = (int)((f0 + e) % TO_RING);
+      const uint32_t buf = (uint32_t)(waited & 1);
+      const bool w = tc_wait(&mbar[buf], (uint32_t)((waited >> 1) & 1), abort_s);
+      waited++;
+      uint32_t r[2][32];
+      if (w) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+          const uint32_t taddr = tmem + ((uint32_t)(32 * q4) << 16) + buf * 128 + (L0 + h) * 32;
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+              "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+              : "=r"(r[h][0]), "=r"(r[h][1]), "=r"(r[h][2]), "=r"(r[h][3]), "=r"(r[h][4]), "=r"(r[h][5]),
+                "=r"(r[h][6]), "=r"(r[h][7]), "=r"(r[h][8]), "=r"(r[h][9]), "=r"(r[h][10]), "=r"(r[h][11]),
+                "=r"(r[h][12]), "=r"(r[h][13]), "=r"(r[h][14]), "=r"(r[h][15]), "=r"(r[h][16]), "=r"(r[h][17]),
+                "=r"(r[h][18]), "=r"(r[h][19]), "=r"(r[h][20]), "=r"(r[h][21]), "=r"(r[h][22]), "=r"(r[h][23]),
+                "=r"(r[h][24]), "=r"(r[h][25]), "=r"(r[h][26]), "=r"(r[h][27]), "=r"(r[h][28]), "=r"(r[h][29]),
+                "=r"(r[h][30]), "=r"(r[h][31])
+              : "r"(taddr));
+        }
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      // TMEM buffer read, the sums of the previous plane done with ds
+      if (!__syncthreads_and(w)) {
+        ok = false;
+        break;
+      }
+      bool oki = true;
+      if (tid == 0 && e + 1 < np) oki = issue(f0 + e + 1);  // overlaps the sums below
+#pragma unroll
+      for (int h = 0; h < 2; h++)
+#pragma unroll
+        for (int tap = 0; tap < NTAP; tap++) ds[((L0 + h) * NTAP + tap) * TC_ROWS + 1 + m] = __uint_as_float(r[h][tap]);
+      if (tid < 8 * NTAP) {  // D of the r-halo cells (rows 0 and 129 of each line) from the staged plane
+        const int hc = tid / NTAP, tap = tid - hc * NTAP, L = hc >> 1, row = (hc & 1) ? TC_ROWS - 1 : 0;
+        const bool wf = tc_wait(&full[s], (uint32_t)(((f0 + e) / TO_RING) & 1), abort_s);
+        float dsum = 0.0f;
+        if (wf) {
+          const unsigned char *src = ring + s * PB + (L * TC_ROWS + row) * 16;
+#pragma unroll
+          for (int slab = 0; slab < 4; slab++) {
+            const uint4 v = *reinterpret_cast<const uint4 *>(src + slab * SLAB);
+            const __nv_bfloat16 *x = reinterpret_cast<const __nv_bfloat16 *>(&v);
+#pragma unroll
+            for (int c = 0; c < 8; c++)
+              dsum = fmaf(__bfloat162float(x[c]), __bfloat162float(a.w[(slab * 8 + c) * NTAP + tap]), dsum);
+          }
+        }
+        oki = oki && wf;
+        ds[(L * NTAP + tap) * TC_ROWS + row] = dsum;
+      }
+      if (!__syncthreads_and(oki)) {  // ds complete; slot s read by its MMAs and the halo
+        ok = false;
+        break;
+      }
+      if (e + TO_RING < np) {  // refill slot s with plane k + TO_RING
+        load(p, k + TO_RING, s);
+        fill++;
+      }
+      // contributions of input plane k: tap (dr, dt, dp) takes D at (i + dr, j + dt) of the
+      // plane k = output plane + dp
+      float c[3];
+#pragma unroll
+      for (int dp = 0; dp < 3; dp++) {
+        float sum = 0.0f;
+#pragma unroll
+        for (int dt = 0; dt < 3; dt++)
+#pragma unroll
+          for (int dr = 0; dr < 3; dr++)
+            sum += ds[((t_out + dt) * NTAP + dp * 9 + dt * 3 + dr) * TC_ROWS + i_out + dr];
+        c[dp] = sum;
+      }
+      acc_prev += c[2];  // output k - 1 (dp = +1): complete now
+      acc_cur += c[1];
+      acc_next += c[0];
+      const int ko = k - 1;
+      if (ko >= p.k0 && ko < p.k1 && p.j0 + t_out < a.g.nth)
+        a.y[(long long)p.b * a.g.nc + ((long long)ko * a.g.nth + p.j0 + t_out) * a.g.nr + p.i0 + i_out] =
+            bias + acc_prev;
+      acc_prev = acc_cur;
+      acc_cur = acc_next;
+      acc_next = 0.0f;
+    }
+  }
+  // teardown: MMAs and copies in flight complete before TMEM is freed and the CTA exits
+  if (tid == 0) {
+    umma_commit(done);
+    tc_drain(done, 0);
+    for (long long fi = fill - 1; fi >= 0 && fi >= fill - TO_RING; fi--)
+      tc_drain(&full[fi % TO_RING], (uint32_t)((fi / TO_RING) & 1));
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (tid == 0 && *abort_s) atomicOr(a.kerr, 1);
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TO_TMEM_COLS));
   }
 }
 
@@ -997,6 +1223,7 @@ int configure_kernels(rkl_ws *ws) {
   if (!rc) rc = set_smem(ws, k_conv_tc<32, EPI_RELU>, tc_smem_bytes<32>());
   if (!rc) rc = set_smem(ws, k_conv_tc<16, EPI_MASK>, tc_smem_bytes<16>());
   if (!rc) rc = set_smem(ws, k_conv_tc<32, EPI_MASK>, tc_smem_bytes<32>());
+  if (!rc) rc = set_smem(ws, k_conv_out_tc, to_smem_bytes());
   return rc;
 }
 
@@ -1078,30 +1305,36 @@ TmapEncodeFn tmap_encoder() {
   return fn;
 }
 
-template <int CIN, int EPI>
-int launch_conv_tc(rkl_ws *ws, const Boxes &g, const __nv_bfloat16 *in, const __nv_bfloat16 *wum, const float *bias,
-                   const __nv_bfloat16 *mask, __nv_bfloat16 *out) {
+// tensor map of a [cells][cin] BF16 activation viewed as {8 channels, r, theta, cin / 8 slabs,
+// box * phi}, box {8, 130, 4, cin / 8, 1}: a box lands in shared memory as
+// [slab][line][r][8 channels]
+int tc_tmap(rkl_ws *ws, const Boxes &g, const __nv_bfloat16 *in, int cin, CUtensorMap *map) {
   const TmapEncodeFn enc = tmap_encoder();
   if (!enc) {
     snprintf(ws->err, sizeof(ws->err), "%s", "cuTensorMapEncodeTiled is not available");
     return RKL_ECUDA;
   }
-  // [box * phi][theta][r][CIN] viewed as {8 channels, r, theta, CIN / 8 slabs, box * phi}, so
-  // that a box lands in shared memory as [slab][line][r][8 channels]
-  CUtensorMap map;
-  const cuuint64_t dims[5] = {8, (cuuint64_t)g.nr, (cuuint64_t)g.nth, (cuuint64_t)(CIN / 8),
+  const cuuint64_t dims[5] = {8, (cuuint64_t)g.nr, (cuuint64_t)g.nth, (cuuint64_t)(cin / 8),
                               (cuuint64_t)g.nbox * (cuuint64_t)g.nph};
-  const cuuint64_t strides[4] = {(cuuint64_t)CIN * 2, (cuuint64_t)g.nr * CIN * 2, 16,
-                                 (cuuint64_t)g.nth * g.nr * CIN * 2};
-  const cuuint32_t box[5] = {8, (cuuint32_t)TC_ROWS, (cuuint32_t)TC_LINES, (cuuint32_t)(CIN / 8), 1};
+  const cuuint64_t strides[4] = {(cuuint64_t)cin * 2, (cuuint64_t)g.nr * cin * 2, 16,
+                                 (cuuint64_t)g.nth * g.nr * cin * 2};
+  const cuuint32_t box[5] = {8, (cuuint32_t)TC_ROWS, (cuuint32_t)TC_LINES, (cuuint32_t)(cin / 8), 1};
   const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
-  const CUresult cr = enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<__nv_bfloat16 *>(in), dims, strides,
+  const CUresult cr = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<__nv_bfloat16 *>(in), dims, strides,
                           box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (cr != CUDA_SUCCESS) {
     snprintf(ws->err, sizeof(ws->err), "cuTensorMapEncodeTiled failed (%d)", (int)cr);
     return RKL_ECUDA;
   }
+  return RKL_OK;
+}
+
+template <int CIN, int EPI>
+int launch_conv_tc(rkl_ws *ws, const Boxes &g, const __nv_bfloat16 *in, const __nv_bfloat16 *wum, const float *bias,
+                   const __nv_bfloat16 *mask, __nv_bfloat16 *out) {
+  CUtensorMap map;
+  if (int rc = tc_tmap(ws, g, in, CIN, &map)) return rc;
   TcArgs a;
   a.g = g;
   a.wum = wum;
@@ -1113,6 +1346,24 @@ int launch_conv_tc(rkl_ws *ws, const Boxes &g, const __nv_bfloat16 *in, const __
   a.kerr = ws->kerr;
   const long long grid = a.nunits < ws->nsm ? a.nunits : ws->nsm;
   k_conv_tc<CIN, EPI><<<(unsigned)grid, TC_THREADS, tc_smem_bytes<CIN>(), ws->stream>>>(map, a);
+  ws->launches += 1;
+  return RKL_OK;
+}
+
+int launch_conv_out_tc(rkl_ws *ws, const Boxes &g, const __nv_bfloat16 *in, const __nv_bfloat16 *w,
+                       const float *bias, float *y) {
+  CUtensorMap map;
+  if (int rc = tc_tmap(ws, g, in, 32, &map)) return rc;
+  ToArgs a;
+  a.g = g;
+  a.w = w;
+  a.bias = bias;
+  a.y = y;
+  a.nchunk = (g.nph + TC_CHUNK - 1) / TC_CHUNK;
+  a.nunits = (long long)g.nbox * (g.nr / TC_R) * ((g.nth + TC_T - 1) / TC_T) * a.nchunk;
+  a.kerr = ws->kerr;
+  const long long grid = a.nunits < ws->nsm ? a.nunits : ws->nsm;
+  k_conv_out_tc<<<(unsigned)grid, TC_THREADS, to_smem_bytes(), ws->stream>>>(map, a);
   ws->launches += 1;
   return RKL_OK;
 }
@@ -1193,6 +1444,7 @@ int run_forward(rkl_ws *ws, const Boxes &g, const Bufs &b) {
     launch_conv<32, 4, EPI_RELU>(ws, g, b.a2, ws->wfrag[2], ws->param + ws->boff[2], nullptr, b.a3);
   }
   if (rc) return rc;
+  if (tc_applies(g)) return launch_conv_out_tc(ws, g, b.a3, ws->wbf + ws->bw_off[3], ws->param + ws->boff[3], b.y);
   launch_conv<32, 1, EPI_F32>(ws, g, b.a3, ws->wfrag[3], ws->param + ws->boff[3], nullptr, b.y);
   return RKL_OK;
 }
