@@ -287,50 +287,66 @@ __global__ void __launch_bounds__(CONV_THREADS, 2) k_conv(ConvArgs a) {
 // ---- tcgen05 implicit-GEMM convolution: CIN in {16, 32} -> 32 channels, grids with nr a
 // multiple of 128 ----
 //
-// A work unit is one column of TC_T = 2 theta rows x 128 r cells of one box, over a chunk of
-// TC_CHUNK phi planes, marched plane by plane.  Each staged plane holds the 4 theta lines
-// (the two rows and their halo) x 130 r cells (with the r halo) of the input, channels-last
-// BF16, in the no-swizzle K-major layout of the tensor-core descriptors: for every 8-channel
-// slab, one 16-byte row per cell, rows contiguous ([slab][line][130 cells][8 channels]).  One
-// 5-D TMA copy brings a plane in (zero fill outside the box in r and theta).  The A operand
-// of a tap is a window of 128 consecutive rows of one staged plane (the tap's shift is an
-// offset of the start address), M = 128 cells; B is the tap's 32 x CIN weight block,
-// resident in shared memory; N = 32, K = 16 per instruction, FP32 accumulators in tensor
-// memory (TMEM).
+// A work unit is one column of TC_T = 2 theta rows x 128 r cells of one box over TC_C = 8
+// consecutive output phi planes.  Its input planes k0 - 1 .. k0 + 8 are staged one by one:
+// the 4 theta lines (the two rows and their halo) x 130 r cells (with the r halo) of the
+// input, channels-last BF16, in the no-swizzle K-major layout of the tensor-core descriptors
+// (for every 8-channel slab one 16-byte row per cell, rows contiguous:
+// [slab][line][130 cells][8 channels]), brought in by one 5-D TMA copy (zero fill outside the
+// box in r and theta).
+//
+// The cost of a tcgen05.mma here is set by the instruction count, not its size, so each MMA
+// carries the three phi taps of one (theta, r) tap: for staged line l, output row t (theta
+// offset dt = l - 1 - t) and r offset dr, A is the window of 128 rows of line l starting at
+// 1 + dr (M = 128 cells, K = 16 channels per instruction) and B stacks the weights of
+// (dt, dr, dp = +1, 0, -1) for the 32 output channels (N = 96), so that one instruction adds
+// input plane k into the accumulators of output planes k - 1, k, k + 1.  TMEM holds the
+// unit's 8 output planes x 2 rows x 32 FP32 channels ([row][plane][channel], all 512
+// columns), so the three planes are adjacent columns (at the ends of a unit the window is cut
+// to 64 or 32 columns).  36 MMAs per input plane, 45 per output plane instead of 108.
 //
 // The CTA is warp-specialised and its roles meet only at mbarriers:
-//   warp 0     loads planes into a ring of TC_RING slots (full[s] / empty[s]);
-//   warp 1     one thread issues the 2 tiles x 27 taps x CIN/16 MMAs of a plane into one of
-//              two TMEM accumulator buffers (tfull[b] / tempty[b]) and, by a commit, frees
-//              the slot of the plane that no later MMA reads;
+//   warp 0     loads input planes into a ring of TC_RING slots (full[s] / empty[s]);
+//   warp 1     one thread issues the MMAs of each input plane, frees its ring slot by a
+//              commit, and commits output plane q as complete (tfull[q]) after input plane
+//              q + 1;
 //   warp 2     allocates and frees the TMEM columns;
-//   warps 4-7  epilogue: TMEM -> registers (warp w reads TMEM lanes 32 (w mod 4) ..), bias +
-//              ReLU or the ReLU mask of the adjoint, BF16 stores.
+//   warps 4-7  epilogue: TMEM -> registers (warp w reads TMEM lanes 32 (w mod 4) ..), then
+//              zeros the plane's columns for the next unit (all MMAs accumulate) and frees
+//              them (tempty[q]); bias + ReLU or the ReLU mask of the adjoint, BF16 stores.
 // Every wait is bounded; one that runs out raises a shared abort flag that ends all roles,
 // the kernel error word is set, and the CTA waits (bounded) for its copies and MMAs in
 // flight before it frees TMEM and returns.
 constexpr int TC_R = 128, TC_T = 2, TC_LINES = TC_T + 2, TC_ROWS = TC_R + 2, TC_PROWS = TC_LINES * TC_ROWS;
-constexpr int TC_RING = 5, TC_THREADS = 256, TC_CHUNK = 32, TC_TMEM_COLS = 128;
+constexpr int TC_RING = 5, TC_THREADS = 256, TC_C = 8, TC_TMEM_COLS = 512;
+constexpr int TC_CHUNK = 32;  // phi planes per unit of the output layer (k_conv_out_tc)
 constexpr long long TC_WAIT = 4000000000LL;  // ~2 s at the maximum SM clock
 
 template <int CIN> constexpr int tc_wbytes() { return NTAP * (CIN / 8) * 32 * 16; }
 template <int CIN> constexpr int tc_plane_bytes() { return (CIN / 8) * TC_PROWS * 16; }
 // weights, ring, 128 bytes of alignment slack, bias + barriers + TMEM slot + abort flag
-template <int CIN> constexpr int tc_smem_bytes() { return tc_wbytes<CIN>() + TC_RING * tc_plane_bytes<CIN>() + 384; }
+// (at least 120000 bytes, so that one CTA, which holds all 512 TMEM columns, runs per SM)
+template <int CIN> constexpr int tc_smem_bytes() {
+  return tc_wbytes<CIN>() + TC_RING * tc_plane_bytes<CIN>() + 512 > 120000
+             ? tc_wbytes<CIN>() + TC_RING * tc_plane_bytes<CIN>() + 512
+             : 120000;
+}
 
 __device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
   return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
          ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
 }
-// kind::f16 instruction descriptor: FP32 accumulate, BF16 A and B, both K-major, M = 128, N = 32
-constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | (4u << 17) | (8u << 24);
+// kind::f16 instruction descriptor: FP32 accumulate, BF16 A and B, both K-major, M = 128, N
+__host__ __device__ constexpr uint32_t tc_idesc(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | (8u << 24);
+}
 
-// D[tmem] (+)= A B^T, M = 128, N = 32, K = 16, BF16 in, FP32 accumulate
-__device__ __forceinline__ void umma_bf16(uint32_t d, uint64_t ad, uint64_t bd, uint32_t acc) {
+// D[tmem] (+)= A B^T, M = 128, K = 16, N from the instruction descriptor, BF16 in, FP32 accumulate
+__device__ __forceinline__ void umma_bf16(uint32_t d, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-      "l"(ad), "l"(bd), "r"(TC_IDESC), "r"(acc));
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
 }
 // arrive on `bar` once every tcgen05 operation this thread has issued so far has completed
 __device__ __forceinline__ void umma_commit(uint64_t *bar) {
@@ -385,6 +401,29 @@ __device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *map, i
       : "memory");
 }
 
+// 32 consecutive TMEM columns of this thread's lane (32x32b shape, one lane per thread)
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+// store 32 consecutive TMEM columns of this thread's lane
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+      "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+      "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]),
+      "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]),
+      "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+      : "memory");
+}
+
 struct TcArgs {
   Boxes g;
   const __nv_bfloat16 *wum;   // [27][CIN / 8][32][8] weight blocks (rows = output channel)
@@ -400,7 +439,7 @@ struct TcUnit {
   int b, i0, j0, k0, k1;
 };
 // unit -> (box, theta pair, r segment, phi chunk), the chunk fastest
-__device__ __forceinline__ TcUnit tc_unit(const Boxes &g, int nchunk, long long u) {
+__device__ __forceinline__ TcUnit tc_unit(const Boxes &g, int nchunk, int chunk, long long u) {
   TcUnit p;
   const int ch = (int)(u % nchunk);
   u /= nchunk;
@@ -411,8 +450,8 @@ __device__ __forceinline__ TcUnit tc_unit(const Boxes &g, int nchunk, long long 
   p.b = (int)(u / npair);
   p.i0 = seg * TC_R;
   p.j0 = pair * TC_T;
-  p.k0 = ch * TC_CHUNK;
-  p.k1 = min(g.nph, p.k0 + TC_CHUNK);
+  p.k0 = ch * chunk;
+  p.k1 = min(g.nph, p.k0 + chunk);
   return p;
 }
 
@@ -421,16 +460,17 @@ __device__ __forceinline__ TcUnit tc_unit(const Boxes &g, int nchunk, long long 
 template <int CIN, int EPI>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(const __grid_constant__ CUtensorMap in, TcArgs a) {
   constexpr int NS = CIN / 8, PB = tc_plane_bytes<CIN>(), SLAB = TC_PROWS * 16;
+  constexpr int BSLAB = 96 * 16, BBLK = NS * BSLAB;  // B block of one (dt, dr): [slab][96 rows][8 channels]
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
-  unsigned char *wsm = smem;                      // weights
+  unsigned char *wsm = smem;                      // weights, 9 B blocks
   unsigned char *ring = smem + tc_wbytes<CIN>();  // TC_RING staged planes
   float *bias_s = reinterpret_cast<float *>(ring + TC_RING * PB);
   uint64_t *full = reinterpret_cast<uint64_t *>(bias_s + 32);
   uint64_t *empty = full + TC_RING;
-  uint64_t *tfull = empty + TC_RING;
-  uint64_t *tempty = tfull + 2;
-  uint64_t *done = tempty + 2;
+  uint64_t *tfull = empty + TC_RING;  // [TC_C]
+  uint64_t *tempty = tfull + TC_C;    // [TC_C]
+  uint64_t *done = tempty + TC_C;
   uint32_t *tslot = reinterpret_cast<uint32_t *>(done + 1);
   volatile int *abort_s = reinterpret_cast<volatile int *>(tslot + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -445,9 +485,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(const __grid_constant
       tc_bar_init(&full[s], 1);
       tc_bar_init(&empty[s], 1);
     }
-    for (int b = 0; b < 2; b++) {
-      tc_bar_init(&tfull[b], 1);
-      tc_bar_init(&tempty[b], 4);
+    for (int q = 0; q < TC_C; q++) {
+      tc_bar_init(&tfull[q], 1);
+      tc_bar_init(&tempty[q], 4);
     }
     tc_bar_init(done, 1);
     *abort_s = 0;
@@ -464,13 +504,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(const __grid_constant
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tslot;
+  if (warp >= 4) {  // the accumulators start at zero (every MMA accumulates)
+    uint32_t z[32];
+#pragma unroll
+    for (int c = 0; c < 32; c++) z[c] = 0u;
+    for (int c0 = 0; c0 < TC_TMEM_COLS; c0 += 32) tmem_st32(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + c0, z);
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
   if (warp == 0) {
     // ---- producer: planes k0 - 1 .. k1 of each unit, fill f into slot f mod TC_RING ----
     long long f = 0;
     bool ok = true;
     for (long long u = blockIdx.x; u < a.nunits && ok; u += gridDim.x) {
-      const TcUnit p = tc_unit(a.g, a.nchunk, u);
+      const TcUnit p = tc_unit(a.g, a.nchunk, TC_C, u);
       for (int k = p.k0 - 1; k <= p.k1; k++, f++) {
         const int s = (int)(f % TC_RING);
         bool w = true;
@@ -506,69 +556,74 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(const __grid_constant
   } else if (warp == 1) {
     // ---- MMA issuer ----
     if (lane == 0) {
-      long long f = 0, gstep = 0;  // fill of the unit's plane k0 - 1; planes issued
+      long long f = 0;    // fill of the unit's input plane k0 - 1
+      uint32_t par = 0;   // bit q: uses of output slot q so far, mod 2
       bool ok = true;
       for (long long u = blockIdx.x; u < a.nunits && ok; u += gridDim.x) {
-        const TcUnit p = tc_unit(a.g, a.nchunk, u);
-        const int nk = p.k1 - p.k0;
-        for (int s = 0; s < nk; s++, gstep++) {
-          // planes k - 1, k, k + 1 are fills f + s .. f + s + 2
-          const int lo = s == 0 ? 0 : 2;
-          for (int e = lo; e < 3 && ok; e++)
-            ok = tc_wait(&full[(f + s + e) % TC_RING], (uint32_t)(((f + s + e) / TC_RING) & 1), abort_s);
-          const uint32_t buf = (uint32_t)(gstep & 1);
-          if (ok) ok = tc_wait(&tempty[buf], (uint32_t)((gstep >> 1) & 1) ^ 1u, abort_s);
+        const TcUnit p = tc_unit(a.g, a.nchunk, TC_C, u);
+        const int nc = p.k1 - p.k0;  // output planes of the unit
+        uint32_t ready = 0;          // output slots known free in this unit
+        for (int qi = -1; qi <= nc && ok; qi++) {  // input plane k0 + qi
+          const long long fi = f + qi + 1;
+          const int s = (int)(fi % TC_RING);
+          ok = tc_wait(&full[s], (uint32_t)((fi / TC_RING) & 1), abort_s);
+          // output planes lo .. hi take this input plane (dp = input - output = +1, 0, -1)
+          const int lo = qi - 1 > 0 ? qi - 1 : 0, hi = qi + 1 < nc - 1 ? qi + 1 : nc - 1;
+          for (int q = lo; q <= hi && ok; q++)
+            if (!((ready >> q) & 1u)) {
+              ok = tc_wait(&tempty[q], ((par >> q) & 1u) ^ 1u, abort_s);
+              ready |= 1u << q;
+            }
           if (!ok) break;
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          // descriptors of the three planes a tap reads and of the weights; a tap's operand is
-          // a constant offset from them (shared addresses stay below 2^18 bytes, so adding
-          // offset >> 4 to the 14-bit start field never carries into the next field)
-          uint64_t ad0[3];
+          const uint32_t idesc = tc_idesc(32 * (hi - lo + 1));
+          const uint32_t brow = (uint32_t)(lo - (qi - 1)) * 32;  // first B row: dp = +1, 0, -1 blocks of 32
+          const uint64_t ad0 = umma_desc(ring_u + (uint32_t)s * PB, SLAB, 128);
+          const uint64_t bd0 = umma_desc(wsm_u + brow * 16, BSLAB, 128);
 #pragma unroll
-          for (int dp = 0; dp < 3; dp++)
-            ad0[dp] = umma_desc(ring_u + (uint32_t)((f + s + dp) % TC_RING) * PB, SLAB, 128);
-          const uint64_t bd0 = umma_desc(wsm_u, 512, 128);
+          for (int l = 0; l < TC_LINES; l++)
 #pragma unroll
-          for (int t = 0; t < TC_T; t++) {
-            const uint32_t d = tmem + buf * 64 + t * 32;
+            for (int t = 0; t < TC_T; t++) {
+              const int dt = l - 1 - t;
+              if (dt < -1 || dt > 1) continue;
 #pragma unroll
-            for (int tap = 0; tap < NTAP; tap++) {
-              const int dr = tap % 3 - 1, dt = (tap / 3) % 3 - 1, dp = tap / 9;
-              const uint32_t arow = (uint32_t)((t + 1 + dt) * TC_ROWS + 1 + dr);
+              for (int dr = -1; dr <= 1; dr++)
 #pragma unroll
-              for (int ks = 0; ks < CIN / 16; ks++) {
-                const uint64_t ad = ad0[dp] + ((arow * 16 + 2 * ks * SLAB) >> 4);
-                const uint64_t bd = bd0 + (((tap * NS + 2 * ks) * 512) >> 4);
-                umma_bf16(d, ad, bd, (tap > 0 || ks > 0) ? 1u : 0u);
-              }
+                for (int ks = 0; ks < CIN / 16; ks++) {
+                  const uint64_t ad = ad0 + ((uint32_t)((l * TC_ROWS + 1 + dr) * 16 + 2 * ks * SLAB) >> 4);
+                  const uint64_t bd = bd0 + ((uint32_t)(((dt + 1) * 3 + (dr + 1)) * BBLK + 2 * ks * BSLAB) >> 4);
+                  umma_bf16(tmem + t * (TC_C * 32) + lo * 32, ad, bd, idesc, 1u);
+                }
             }
-          }
-          umma_commit(&tfull[buf]);
-          umma_commit(&empty[(f + s) % TC_RING]);  // plane k - 1: no later MMA of the unit reads it
+          umma_commit(&empty[s]);                    // this input plane is read
+          if (qi >= 1) umma_commit(&tfull[qi - 1]);  // output plane qi - 1 has all its inputs
         }
         if (!ok) break;
-        umma_commit(&empty[(f + nk) % TC_RING]);  // the unit's last two planes
-        umma_commit(&empty[(f + nk + 1) % TC_RING]);
-        f += nk + 2;
+        par ^= (1u << nc) - 1u;
+        f += nc + 2;
       }
       umma_commit(done);  // teardown: every MMA issued has completed
       tc_drain(done, 0);
     }
     __syncwarp();
   } else if (warp >= 4) {
-    // ---- epilogue: plane k from TMEM buffer gstep & 1 ----
+    // ---- epilogue: output plane k0 + q from TMEM slot q ----
     const int q4 = warp & 3, m = 32 * q4 + lane;
-    long long gstep = 0;
+    uint32_t par = 0;
     bool ok = true;
+    uint32_t z[32];
+#pragma unroll
+    for (int c = 0; c < 32; c++) z[c] = 0u;
     for (long long u = blockIdx.x; u < a.nunits && ok; u += gridDim.x) {
-      const TcUnit p = tc_unit(a.g, a.nchunk, u);
-      for (int k = p.k0; k < p.k1; k++, gstep++) {
-        const uint32_t buf = (uint32_t)(gstep & 1);
+      const TcUnit p = tc_unit(a.g, a.nchunk, TC_C, u);
+      const int nc = p.k1 - p.k0;
+      const bool row1 = p.j0 + 1 < a.g.nth;  // an odd theta count leaves the last pair one row
+      for (int q = 0; q < nc; q++) {
+        const int k = p.k0 + q;
         long long cell[TC_T];
 #pragma unroll
         for (int t = 0; t < TC_T; t++)
           cell[t] = (long long)p.b * a.g.nc + ((long long)k * a.g.nth + (p.j0 + t)) * a.g.nr + p.i0 + m;
-        const bool row1 = p.j0 + 1 < a.g.nth;  // an odd theta count leaves the last pair one row
         uint4 mk[TC_T][4];
         if (EPI == EPI_MASK) {  // issued before the wait, so that their latency hides behind it
 #pragma unroll
@@ -578,7 +633,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(const __grid_constant
               mk[t][v] = (t == 0 || row1) ? reinterpret_cast<const uint4 *>(a.mask + cell[t] * 32)[v]
                                           : make_uint4(0, 0, 0, 0);
         }
-        const bool w = tc_wait(&tfull[buf], (uint32_t)((gstep >> 1) & 1), abort_s);
+        const bool w = tc_wait(&tfull[q], (par >> q) & 1u, abort_s);
         if (!__all_sync(0xffffffffu, w)) {
           ok = false;
           break;
@@ -586,31 +641,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(const __grid_constant
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         uint32_t r[TC_T][32];
 #pragma unroll
-        for (int t = 0; t < TC_T; t++) {
-          const uint32_t taddr = tmem + ((uint32_t)(32 * q4) << 16) + buf * 64 + t * 32;
-          asm volatile(
-              "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-              "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-              : "=r"(r[t][0]), "=r"(r[t][1]), "=r"(r[t][2]), "=r"(r[t][3]), "=r"(r[t][4]), "=r"(r[t][5]),
-                "=r"(r[t][6]), "=r"(r[t][7]), "=r"(r[t][8]), "=r"(r[t][9]), "=r"(r[t][10]), "=r"(r[t][11]),
-                "=r"(r[t][12]), "=r"(r[t][13]), "=r"(r[t][14]), "=r"(r[t][15]), "=r"(r[t][16]), "=r"(r[t][17]),
-                "=r"(r[t][18]), "=r"(r[t][19]), "=r"(r[t][20]), "=r"(r[t][21]), "=r"(r[t][22]), "=r"(r[t][23]),
-                "=r"(r[t][24]), "=r"(r[t][25]), "=r"(r[t][26]), "=r"(r[t][27]), "=r"(r[t][28]), "=r"(r[t][29]),
-                "=r"(r[t][30]), "=r"(r[t][31])
-              : "r"(taddr));
-        }
+        for (int t = 0; t < TC_T; t++) tmem_ld32(tmem + ((uint32_t)(32 * q4) << 16) + t * (TC_C * 32) + q * 32, r[t]);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int t = 0; t < TC_T; t++) tmem_st32(tmem + ((uint32_t)(32 * q4) << 16) + t * (TC_C * 32) + q * 32, z);
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncwarp();
-        if (lane == 0) tc_arrive(&tempty[buf]);  // the MMAs of plane k + 2 may overwrite it
+        if (lane == 0) tc_arrive(&tempty[q]);  // slot q is zero again: the next unit may accumulate
 #pragma unroll
         for (int t = 0; t < TC_T; t++) {
           if (t > 0 && !row1) break;
           __align__(16) __nv_bfloat16 o[32];
           if (EPI == EPI_RELU) {
 #pragma unroll
-            for (int c = 0; c < 32; c++)
-              o[c] = __float2bfloat16_rn(fmaxf(__uint_as_float(r[t][c]) + bias_s[c], 0.0f));
+            for (int c = 0; c < 32; c++) o[c] = __float2bfloat16_rn(fmaxf(__uint_as_float(r[t][c]) + bias_s[c], 0.0f));
           } else {
             const __nv_bfloat16 *mb = reinterpret_cast<const __nv_bfloat16 *>(mk[t]);
 #pragma unroll
@@ -622,6 +667,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(const __grid_constant
           for (int v = 0; v < 4; v++) dst[v] = reinterpret_cast<const uint4 *>(o)[v];
         }
       }
+      par ^= (1u << nc) - 1u;
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -736,14 +782,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_out_tc(const __grid_cons
       for (int ks = 0; ks < 2; ks++)
         umma_bf16(tmem + buf * 128 + L * 32,
                   umma_desc(ring_u + s * PB + (L * TC_ROWS + 1) * 16 + 2 * ks * SLAB, SLAB, 128),
-                  umma_desc(wb_u + 2 * ks * 512, 512, 128), ks > 0 ? 1u : 0u);
+                  umma_desc(wb_u + 2 * ks * 512, 512, 128), tc_idesc(32), ks > 0 ? 1u : 0u);
     umma_commit(&mbar[buf]);
     gm++;
     return true;
   };
 
   for (long long u = blockIdx.x; u < a.nunits && ok; u += gridDim.x) {
-    const TcUnit p = tc_unit(a.g, a.nchunk, u);
+    const TcUnit p = tc_unit(a.g, a.nchunk, TC_CHUNK, u);
     const int np = p.k1 - p.k0 + 2;  // input planes k0 - 1 .. k1
     const long long f0 = fill;
     for (int e = 0; e < TO_RING && e < np; e++) load(p, p.k0 - 1 + e, (int)((f0 + e) % TO_RING));
@@ -1013,23 +1059,26 @@ __global__ void k_wfrag(const __nv_bfloat16 *__restrict__ w, int cin, int cout, 
   out[idx] = make_uint2(pack(2 * q), pack(2 * q + 8));
 }
 
-// B blocks of the tcgen05 convolution, [tap][cin / 8][32][8] (row n = output channel of the
-// convolution, 8 consecutive input channels): forward B[n][k] = W[n][k][tap]; adjoint
-// B[n][k] = W[k][n][26 - tap].  Channels beyond the layer's real counts are zero.
+// B blocks of the tcgen05 convolution, [dt + 1][dr + 1][cin / 8][96][8]: row n = 32 dpi + c with
+// dp = 1 - dpi (the phi offsets +1, 0, -1 in that order) and c the output channel of the
+// convolution, 8 consecutive input channels per 16-byte row; forward B[n][k] = W[c][k][tap],
+// adjoint B[n][k] = W[k][c][26 - tap], tap = (dr + 1) + 3 (dt + 1) + 9 (dp + 1).  Channels
+// beyond the layer's real counts are zero.
 __global__ void k_wumma(const __nv_bfloat16 *__restrict__ w, int cin, int cout, int CIN, int adjoint,
                         __nv_bfloat16 *__restrict__ out) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= NTAP * CIN * 32) return;
-  const int e = idx % 8, n = (idx / 8) % 32, slab = (idx / 256) % (CIN / 8), tap = idx / (256 * (CIN / 8));
-  const int k = slab * 8 + e;
+  const int e = idx % 8, n = (idx / 8) % 96, slab = (idx / 768) % (CIN / 8), blk = idx / (768 * (CIN / 8));
+  const int dti = blk / 3, dri = blk % 3, dpi = n / 32, c = n % 32, k = slab * 8 + e;
+  const int tap = dri + 3 * dti + 9 * (2 - dpi);
   int co, ci, t;
   if (!adjoint) {
-    co = n;
+    co = c;
     ci = k;
     t = tap;
   } else {
     co = k;
-    ci = n;
+    ci = c;
     t = NTAP - 1 - tap;
   }
   out[idx] = (co < cout && ci < cin) ? w[((size_t)co * cin + ci) * NTAP + t] : __float2bfloat16(0.0f);
@@ -1341,7 +1390,7 @@ int launch_conv_tc(rkl_ws *ws, const Boxes &g, const __nv_bfloat16 *in, const __
   a.bias = bias;
   a.mask = mask;
   a.out = out;
-  a.nchunk = (g.nph + TC_CHUNK - 1) / TC_CHUNK;
+  a.nchunk = (g.nph + TC_C - 1) / TC_C;
   a.nunits = (long long)g.nbox * (g.nr / TC_R) * ((g.nth + TC_T - 1) / TC_T) * a.nchunk;
   a.kerr = ws->kerr;
   const long long grid = a.nunits < ws->nsm ? a.nunits : ws->nsm;
