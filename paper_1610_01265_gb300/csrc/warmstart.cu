@@ -148,16 +148,24 @@ __device__ __forceinline__ long long cell_index(const Boxes &g, int b, int i, in
   return (long long)b * g.nc + ((long long)k * g.nth + j) * g.nr + i;
 }
 
+// 8 channels (16 bytes) c of a cell of a C-channel BF16 activation: channels-last
+// [cells][C] when ss = 0, else planar 8-channel slabs [C / 8][cells][8] with slab stride ss
+// elements (the layout of the grids on the tcgen05 path)
+__device__ __forceinline__ const __nv_bfloat16 *chunk_ptr(const __nv_bfloat16 *src, long long cell, int c, int C,
+                                                          long long ss) {
+  return ss ? src + c * ss + cell * 8 : src + cell * C + c * 8;
+}
+
 // stage the brick's halo rows of a C-channel activation (zero outside the box)
 template <int C>
 __device__ __forceinline__ void stage_halo(const Boxes &g, const BrickPos &p, const __nv_bfloat16 *src,
-                                           unsigned char *halo) {
+                                           unsigned char *halo, long long ss = 0) {
   constexpr int NCH = C / 8;
   for (int q = threadIdx.x; q < NH * NCH; q += blockDim.x) {
     const int h = q / NCH, c = q - h * NCH;
     const int hr = h % HR, ht = (h / HR) % HT, hp = h / (HR * HT);
     const long long cell = cell_index(g, p.b, p.i0 + hr - 1, p.j0 + ht - 1, p.k0 + hp - 1);
-    const __nv_bfloat16 *gp = cell >= 0 ? src + cell * C + c * 8 : src;
+    const __nv_bfloat16 *gp = cell >= 0 ? chunk_ptr(src, cell, c, C, ss) : src;
     cp_async16(halo + h * (C * 2) + ((c ^ swz<C>(h)) << 4), gp, cell >= 0 ? 16 : 0);
   }
 }
@@ -165,14 +173,14 @@ __device__ __forceinline__ void stage_halo(const Boxes &g, const BrickPos &p, co
 // stage the brick's own rows of a C-channel tensor (zero outside the box)
 template <int C>
 __device__ __forceinline__ void stage_brick(const Boxes &g, const BrickPos &p, const __nv_bfloat16 *src,
-                                            unsigned char *dst) {
+                                            unsigned char *dst, long long ss = 0) {
   constexpr int NCH = C / 8;
   for (int q = threadIdx.x; q < BRICK * NCH; q += blockDim.x) {
     const int r = q / NCH, c = q - r * NCH;
     const int ir = r % BR, it = (r / BR) % BT, ip = r / (BR * BT);
     const int i = p.i0 + ir, j = p.j0 + it, k = p.k0 + ip;
     const long long cell = (k < g.nph) ? cell_index(g, p.b, i, j, k) : -1;
-    const __nv_bfloat16 *gp = cell >= 0 ? src + cell * C + c * 8 : src;
+    const __nv_bfloat16 *gp = cell >= 0 ? chunk_ptr(src, cell, c, C, ss) : src;
     cp_async16(dst + r * (C * 2) + ((c ^ swz<C>(r)) << 4), gp, cell >= 0 ? 16 : 0);
   }
 }
@@ -307,9 +315,10 @@ __global__ void __launch_bounds__(CONV_THREADS, 2) k_conv(ConvArgs a) {
 //
 // The CTA is warp-specialised and its roles meet only at mbarriers:
 //   warp 0     loads input planes into a ring of TC_RING slots (full[s] / empty[s]);
-//   warp 1     one thread issues the MMAs of each input plane, frees its ring slot by a
-//              commit, and commits output plane q as complete (tfull[q]) after input plane
-//              q + 1;
+//   warps 1, 3 one thread each issues the MMAs of one output row for each input plane (two
+//              issuers, as the issue of a tcgen05.mma, not its execution, sets the rate here),
+//              frees the plane's ring slot by a commit, and commits output plane q as
+//              complete (tfull[q]) after input plane q + 1;
 //   warp 2     allocates and frees the TMEM columns;
 //   warps 4-7  epilogue: TMEM -> registers (warp w reads TMEM lanes 32 (w mod 4) ..), then
 //              zeros the plane's columns for the next unit (all MMAs accumulate) and frees
@@ -430,6 +439,7 @@ struct TcArgs {
   const float *bias;          // [32] (EPI_RELU) or NULL
   const __nv_bfloat16 *mask;  // [cells][32] (EPI_MASK)
   __nv_bfloat16 *out;         // [cells][32]
+  long long ss;               // slab stride of mask and out (planar [4][cells][8])
   long long nunits;
   int nchunk;                 // phi chunks per column
   int *kerr;                  // set when a bounded wait runs out
@@ -470,8 +480,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(const __grid_constant
   uint64_t *empty = full + TC_RING;
   uint64_t *tfull = empty + TC_RING;  // [TC_C]
   uint64_t *tempty = tfull + TC_C;    // [TC_C]
-  uint64_t *done = tempty + TC_C;
-  uint32_t *tslot = reinterpret_cast<uint32_t *>(done + 1);
+  uint64_t *done = tempty + TC_C;  // [2], one per MMA issuer
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(done + 2);
   volatile int *abort_s = reinterpret_cast<volatile int *>(tslot + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t wsm_u = smem_u32(wsm), ring_u = smem_u32(ring);
@@ -483,13 +493,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(const __grid_constant
   if (tid == 0) {
     for (int s = 0; s < TC_RING; s++) {
       tc_bar_init(&full[s], 1);
-      tc_bar_init(&empty[s], 1);
+      tc_bar_init(&empty[s], TC_T);  // one commit per MMA issuer
     }
     for (int q = 0; q < TC_C; q++) {
-      tc_bar_init(&tfull[q], 1);
+      tc_bar_init(&tfull[q], TC_T);
       tc_bar_init(&tempty[q], 4);
     }
-    tc_bar_init(done, 1);
+    tc_bar_init(&done[0], 1);
+    tc_bar_init(&done[1], 1);
     *abort_s = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -553,8 +564,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(const __grid_constant
     if (lane == 0)
       for (long long fi = f - 1; fi >= 0 && fi >= f - TC_RING; fi--)
         tc_drain(&full[fi % TC_RING], (uint32_t)((fi / TC_RING) & 1));
-  } else if (warp == 1) {
-    // ---- MMA issuer ----
+  } else if (warp == 1 || warp == 3) {
+    // ---- MMA issuers: warp 1 the MMAs of output row 0, warp 3 those of row 1 ----
+    const int tt = warp == 1 ? 0 : 1;
     if (lane == 0) {
       long long f = 0;    // fill of the unit's input plane k0 - 1
       uint32_t par = 0;   // bit q: uses of output slot q so far, mod 2
@@ -585,7 +597,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(const __grid_constant
 #pragma unroll
             for (int t = 0; t < TC_T; t++) {
               const int dt = l - 1 - t;
-              if (dt < -1 || dt > 1) continue;
+              if (t != tt || dt < -1 || dt > 1) continue;
 #pragma unroll
               for (int dr = -1; dr <= 1; dr++)
 #pragma unroll
@@ -602,8 +614,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(const __grid_constant
         par ^= (1u << nc) - 1u;
         f += nc + 2;
       }
-      umma_commit(done);  // teardown: every MMA issued has completed
-      tc_drain(done, 0);
+      umma_commit(&done[tt]);  // teardown: every MMA issued has completed
+      tc_drain(&done[tt], 0);
     }
     __syncwarp();
   } else if (warp >= 4) {
@@ -630,7 +642,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(const __grid_constant
           for (int t = 0; t < TC_T; t++)
 #pragma unroll
             for (int v = 0; v < 4; v++)
-              mk[t][v] = (t == 0 || row1) ? reinterpret_cast<const uint4 *>(a.mask + cell[t] * 32)[v]
+              mk[t][v] = (t == 0 || row1) ? *reinterpret_cast<const uint4 *>(a.mask + v * a.ss + cell[t] * 8)
                                           : make_uint4(0, 0, 0, 0);
         }
         const bool w = tc_wait(&tfull[q], (par >> q) & 1u, abort_s);
@@ -662,9 +674,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(const __grid_constant
             for (int c = 0; c < 32; c++)
               o[c] = __float2bfloat16_rn(__bfloat162float(mb[c]) > 0.0f ? __uint_as_float(r[t][c]) : 0.0f);
           }
-          uint4 *dst = reinterpret_cast<uint4 *>(a.out + cell[t] * 32);
 #pragma unroll
-          for (int v = 0; v < 4; v++) dst[v] = reinterpret_cast<const uint4 *>(o)[v];
+          for (int v = 0; v < 4; v++)
+            *reinterpret_cast<uint4 *>(a.out + v * a.ss + cell[t] * 8) = reinterpret_cast<const uint4 *>(o)[v];
         }
       }
       par ^= (1u << nc) - 1u;
@@ -687,12 +699,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(const __grid_constant
 // y(x) = bias + sum_tap D[x + d(tap)][tap]: every input is multiplied once, not once per tap.
 // Units and staging are those of k_conv_tc (one 5-D TMA copy per plane, ring of TO_RING);
 // D of the two r-halo cells of each line (outside the 128-cell tile) is formed on the CUDA
-// cores.  TMEM holds D of two planes, so the MMAs of plane k + 1 run while the sums of plane k
-// are formed: input plane k adds its contributions to the outputs of planes k - 1, k, k + 1,
-// held in registers, one output cell per thread.
-constexpr int TO_RING = 3, TO_TMEM_COLS = 256;
+// cores.  Input plane k adds its contributions to the outputs of planes k - 1, k, k + 1, held
+// in registers, one output cell per thread.
+//
+// Roles, synchronised by bounded mbarrier waits as in k_conv_tc:
+//   warp 0     TMA producer (ring slot s is free once the MMAs of its plane and the r-halo
+//              sums that read it are done: empty[s] takes two arrivals);
+//   warp 1     allocates TMEM and issues the 8 MMAs of each plane into one of TO_NBUF TMEM
+//              buffers (tfull / tempty), running up to TO_NBUF - 1 planes ahead;
+//   warps 2-9  math: TMEM -> D tile in shared memory (double-buffered), r-halo D, one named
+//              barrier per plane (which also ANDs the waits' outcomes, so that all math warps
+//              leave together if one wait gives up), the 27-tap sums and the y stores.
+constexpr int TO_RING = 3, TO_NBUF = 4, TO_TMEM_COLS = 512, TO_THREADS = 320;
 constexpr int TO_DS_FLOATS = TC_LINES * NTAP * TC_ROWS;  // D of one plane, [line][tap][130 cells]
-constexpr int to_smem_bytes() { return TO_RING * tc_plane_bytes<32>() + TO_DS_FLOATS * 4 + 2048 + 384; }
+constexpr int to_smem_bytes() { return TO_RING * tc_plane_bytes<32>() + 2 * TO_DS_FLOATS * 4 + 2048 + 512; }
 
 struct ToArgs {
   Boxes g;
@@ -704,35 +724,53 @@ struct ToArgs {
   int *kerr;
 };
 
-__global__ void __launch_bounds__(TC_THREADS, 1) k_conv_out_tc(const __grid_constant__ CUtensorMap in, ToArgs a) {
+// barrier 1 over the 256 math threads; returns the AND of v over them
+__device__ __forceinline__ bool math_bar_and(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.and.pred q, 1, 256, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)v)
+      : "memory");
+  return r != 0;
+}
+
+__global__ void __launch_bounds__(TO_THREADS, 1) k_conv_out_tc(const __grid_constant__ CUtensorMap in, ToArgs a) {
   constexpr int PB = tc_plane_bytes<32>(), SLAB = TC_PROWS * 16;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
-  unsigned char *ring = smem;                                           // TO_RING staged planes
-  float *ds = reinterpret_cast<float *>(ring + TO_RING * PB);           // [4][27][130]
-  __nv_bfloat16 *wb = reinterpret_cast<__nv_bfloat16 *>(ds + TO_DS_FLOATS);  // B: [4 slabs][32 taps][8 ci]
-  uint64_t *full = reinterpret_cast<uint64_t *>(wb + 1024);             // [TO_RING]
-  uint64_t *mbar = full + TO_RING;                                      // [2] MMAs of TMEM buffer b
-  uint64_t *done = mbar + 2;
+  unsigned char *ring = smem;                                      // TO_RING staged planes
+  float *ds0 = reinterpret_cast<float *>(ring + TO_RING * PB);     // 2 x [4][27][130]
+  __nv_bfloat16 *wb = reinterpret_cast<__nv_bfloat16 *>(ds0 + 2 * TO_DS_FLOATS);  // B: [4 slabs][32 taps][8 ci]
+  uint64_t *full = reinterpret_cast<uint64_t *>(wb + 1024);        // [TO_RING]
+  uint64_t *empty = full + TO_RING;                                // [TO_RING]
+  uint64_t *tfull = empty + TO_RING;                               // [TO_NBUF]
+  uint64_t *tempty = tfull + TO_NBUF;                              // [TO_NBUF]
+  uint64_t *done = tempty + TO_NBUF;
   uint32_t *tslot = reinterpret_cast<uint32_t *>(done + 1);
   volatile int *abort_s = reinterpret_cast<volatile int *>(tslot + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t ring_u = smem_u32(ring), wb_u = smem_u32(wb);
   const int nph = a.g.nph;
 
-  for (int q = tid; q < 1024; q += TC_THREADS) {
+  for (int q = tid; q < 1024; q += TO_THREADS) {
     const int slab = q >> 8, n = (q >> 3) & 31, ci = slab * 8 + (q & 7);
     wb[q] = n < NTAP ? a.w[ci * NTAP + n] : __float2bfloat16(0.0f);
   }
   if (tid == 0) {
-    for (int s = 0; s < TO_RING; s++) tc_bar_init(&full[s], 1);
-    tc_bar_init(&mbar[0], 1);
-    tc_bar_init(&mbar[1], 1);
+    for (int s = 0; s < TO_RING; s++) {
+      tc_bar_init(&full[s], 1);
+      tc_bar_init(&empty[s], 2);
+    }
+    for (int b = 0; b < TO_NBUF; b++) {
+      tc_bar_init(&tfull[b], 1);
+      tc_bar_init(&tempty[b], 8);
+    }
     tc_bar_init(done, 1);
     *abort_s = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) {
+  if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
                  "r"(TO_TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -742,164 +780,156 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_out_tc(const __grid_cons
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tslot;
-  const float bias = a.bias[0];
-  const int t_out = tid >> 7, i_out = tid & 127;  // this thread's output cell in the tile
-  const int q4 = warp & 3, m = 32 * q4 + lane;     // TMEM lane = tile cell
-  const int L0 = (warp >> 2) * 2;                  // this warp's two lines of D
 
-  long long fill = 0, gm = 0;  // fills issued; MMA batches committed
-  long long waited = 0;        // MMA batches waited for
-  bool ok = true;
-  // stage plane kk of unit p into slot s (all threads: the zero fill of a plane outside a
-  // non-periodic box is written by the CTA)
-  auto load = [&](const TcUnit &p, int kk, int s) {
-    if (kk < 0 || kk >= nph) {
-      if (a.g.periodic) {
-        kk = ((kk % nph) + nph) % nph;
-      } else {
+  if (warp == 0) {
+    // ---- producer: planes k0 - 1 .. k1 of each unit, fill f into slot f mod TO_RING ----
+    long long f = 0;
+    bool ok = true;
+    for (long long u = blockIdx.x; u < a.nunits && ok; u += gridDim.x) {
+      const TcUnit p = tc_unit(a.g, a.nchunk, TC_CHUNK, u);
+      for (int k = p.k0 - 1; k <= p.k1; k++, f++) {
+        const int s = (int)(f % TO_RING);
+        bool w = true;
+        if (lane == 0) w = tc_wait(&empty[s], (uint32_t)((f / TO_RING) & 1) ^ 1u, abort_s);
+        if (!__shfl_sync(0xffffffffu, w, 0)) {
+          ok = false;
+          break;
+        }
+        int kk = k;
+        bool zero = false;
+        if (kk < 0 || kk >= nph) {
+          if (a.g.periodic) kk = ((kk % nph) + nph) % nph;
+          else zero = true;
+        }
         unsigned char *dst = ring + s * PB;
-        for (int q = tid; q < PB / 16; q += TC_THREADS) reinterpret_cast<uint4 *>(dst)[q] = make_uint4(0, 0, 0, 0);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) tc_arrive(&full[s]);
-        return;
-      }
-    }
-    if (tid == 0) {
-      tc_expect_tx(&full[s], PB);
-      tma_load_5d(ring + s * PB, &in, 0, p.i0 - 1, p.j0 - 1, 0, p.b * nph + kk, &full[s]);
-    }
-  };
-  // thread 0: the 8 MMAs of D for the plane of fill fi into TMEM buffer gm & 1
-  auto issue = [&](long long fi) -> bool {
-    const int s = (int)(fi % TO_RING);
-    if (!tc_wait(&full[s], (uint32_t)((fi / TO_RING) & 1), abort_s)) return false;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t buf = (uint32_t)(gm & 1);
-#pragma unroll
-    for (int L = 0; L < TC_LINES; L++)
-#pragma unroll
-      for (int ks = 0; ks < 2; ks++)
-        umma_bf16(tmem + buf * 128 + L * 32,
-                  umma_desc(ring_u + s * PB + (L * TC_ROWS + 1) * 16 + 2 * ks * SLAB, SLAB, 128),
-                  umma_desc(wb_u + 2 * ks * 512, 512, 128), tc_idesc(32), ks > 0 ? 1u : 0u);
-    umma_commit(&mbar[buf]);
-    gm++;
-    return true;
-  };
-
-  for (long long u = blockIdx.x; u < a.nunits && ok; u += gridDim.x) {
-    const TcUnit p = tc_unit(a.g, a.nchunk, TC_CHUNK, u);
-    const int np = p.k1 - p.k0 + 2;  // input planes k0 - 1 .. k1
-    const long long f0 = fill;
-    for (int e = 0; e < TO_RING && e < np; e++) load(p, p.k0 - 1 + e, (int)((f0 + e) % TO_RING));
-    fill = f0 + (np < TO_RING ? np : TO_RING);
-    bool ok0 = true;
-    if (tid == 0) ok0 = issue(f0);
-    if (!__syncthreads_and(ok0)) {
-      ok = false;
-      break;
-    }
-    float acc_prev = 0.0f, acc_cur = 0.0f, acc_next = 0.0f;  // outputs k - 1, k, k + 1
-    for (int e = 0; e < np; e++) {
-      const int k = p.k0 - 1 + e;
-      const int s = (int)((f0 + e) % TO_RING);
-      const uint32_t buf = (uint32_t)(waited & 1);
-      const bool w = tc_wait(&mbar[buf], (uint32_t)((waited >> 1) & 1), abort_s);
-      waited++;
-      uint32_t r[2][32];
-      if (w) {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll
-        for (int h = 0; h < 2; h++) {
-          const uint32_t taddr = tmem + ((uint32_t)(32 * q4) << 16) + buf * 128 + (L0 + h) * 32;
-          asm volatile(
-              "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-              "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-              : "=r"(r[h][0]), "=r"(r[h][1]), "=r"(r[h][2]), "=r"(r[h][3]), "=r"(r[h][4]), "=r"(r[h][5]),
-                "=r"(r[h][6]), "=r"(r[h][7]), "=r"(r[h][8]), "=r"(r[h][9]), "=r"(r[h][10]), "=r"(r[h][11]),
-                "=r"(r[h][12]), "=r"(r[h][13]), "=r"(r[h][14]), "=r"(r[h][15]), "=r"(r[h][16]), "=r"(r[h][17]),
-                "=r"(r[h][18]), "=r"(r[h][19]), "=r"(r[h][20]), "=r"(r[h][21]), "=r"(r[h][22]), "=r"(r[h][23]),
-                "=r"(r[h][24]), "=r"(r[h][25]), "=r"(r[h][26]), "=r"(r[h][27]), "=r"(r[h][28]), "=r"(r[h][29]),
-                "=r"(r[h][30]), "=r"(r[h][31])
-              : "r"(taddr));
-        }
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      }
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      // TMEM buffer read, the sums of the previous plane done with ds
-      if (!__syncthreads_and(w)) {
-        ok = false;
-        break;
-      }
-      bool oki = true;
-      if (tid == 0 && e + 1 < np) oki = issue(f0 + e + 1);  // overlaps the sums below
-#pragma unroll
-      for (int h = 0; h < 2; h++)
-#pragma unroll
-        for (int tap = 0; tap < NTAP; tap++) ds[((L0 + h) * NTAP + tap) * TC_ROWS + 1 + m] = __uint_as_float(r[h][tap]);
-      if (tid < 8 * NTAP) {  // D of the r-halo cells (rows 0 and 129 of each line) from the staged plane
-        const int hc = tid / NTAP, tap = tid - hc * NTAP, L = hc >> 1, row = (hc & 1) ? TC_ROWS - 1 : 0;
-        const bool wf = tc_wait(&full[s], (uint32_t)(((f0 + e) / TO_RING) & 1), abort_s);
-        float dsum = 0.0f;
-        if (wf) {
-          const unsigned char *src = ring + s * PB + (L * TC_ROWS + row) * 16;
-#pragma unroll
-          for (int slab = 0; slab < 4; slab++) {
-            const uint4 v = *reinterpret_cast<const uint4 *>(src + slab * SLAB);
-            const __nv_bfloat16 *x = reinterpret_cast<const __nv_bfloat16 *>(&v);
-#pragma unroll
-            for (int c = 0; c < 8; c++)
-              dsum = fmaf(__bfloat162float(x[c]), __bfloat162float(a.w[(slab * 8 + c) * NTAP + tap]), dsum);
+        if (!zero) {
+          if (lane == 0) {
+            tc_expect_tx(&full[s], PB);
+            tma_load_5d(dst, &in, 0, p.i0 - 1, p.j0 - 1, 0, p.b * nph + kk, &full[s]);
           }
+        } else {  // outside a non-periodic box: zeros, written by the warp
+          for (int q = lane; q < PB / 16; q += 32) reinterpret_cast<uint4 *>(dst)[q] = make_uint4(0, 0, 0, 0);
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) tc_arrive(&full[s]);
         }
-        oki = oki && wf;
-        ds[(L * NTAP + tap) * TC_ROWS + row] = dsum;
       }
-      if (!__syncthreads_and(oki)) {  // ds complete; slot s read by its MMAs and the halo
-        ok = false;
-        break;
-      }
-      if (e + TO_RING < np) {  // refill slot s with plane k + TO_RING
-        load(p, k + TO_RING, s);
-        fill++;
-      }
-      // contributions of input plane k: tap (dr, dt, dp) takes D at (i + dr, j + dt) of the
-      // plane k = output plane + dp
-      float c[3];
-#pragma unroll
-      for (int dp = 0; dp < 3; dp++) {
-        float sum = 0.0f;
-#pragma unroll
-        for (int dt = 0; dt < 3; dt++)
-#pragma unroll
-          for (int dr = 0; dr < 3; dr++)
-            sum += ds[((t_out + dt) * NTAP + dp * 9 + dt * 3 + dr) * TC_ROWS + i_out + dr];
-        c[dp] = sum;
-      }
-      acc_prev += c[2];  // output k - 1 (dp = +1): complete now
-      acc_cur += c[1];
-      acc_next += c[0];
-      const int ko = k - 1;
-      if (ko >= p.k0 && ko < p.k1 && p.j0 + t_out < a.g.nth)
-        a.y[(long long)p.b * a.g.nc + ((long long)ko * a.g.nth + p.j0 + t_out) * a.g.nr + p.i0 + i_out] =
-            bias + acc_prev;
-      acc_prev = acc_cur;
-      acc_cur = acc_next;
-      acc_next = 0.0f;
     }
-  }
-  // teardown: MMAs and copies in flight complete before TMEM is freed and the CTA exits
-  if (tid == 0) {
-    umma_commit(done);
-    tc_drain(done, 0);
-    for (long long fi = fill - 1; fi >= 0 && fi >= fill - TO_RING; fi--)
-      tc_drain(&full[fi % TO_RING], (uint32_t)((fi / TO_RING) & 1));
+    if (lane == 0)
+      for (long long fi = f - 1; fi >= 0 && fi >= f - TO_RING; fi--)
+        tc_drain(&full[fi % TO_RING], (uint32_t)((fi / TO_RING) & 1));
+  } else if (warp == 1) {
+    // ---- MMA issuer: D of plane g (all units in order) into TMEM buffer g mod TO_NBUF ----
+    if (lane == 0) {
+      long long g = 0;
+      bool ok = true;
+      for (long long u = blockIdx.x; u < a.nunits && ok; u += gridDim.x) {
+        const TcUnit p = tc_unit(a.g, a.nchunk, TC_CHUNK, u);
+        for (int k = p.k0 - 1; k <= p.k1; k++, g++) {
+          const int s = (int)(g % TO_RING), buf = (int)(g % TO_NBUF);
+          ok = tc_wait(&full[s], (uint32_t)((g / TO_RING) & 1), abort_s);
+          if (ok) ok = tc_wait(&tempty[buf], (uint32_t)((g / TO_NBUF) & 1) ^ 1u, abort_s);
+          if (!ok) break;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+          for (int L = 0; L < TC_LINES; L++)
+#pragma unroll
+            for (int ks = 0; ks < 2; ks++)
+              umma_bf16(tmem + buf * 128 + L * 32,
+                        umma_desc(ring_u + s * PB + (L * TC_ROWS + 1) * 16 + 2 * ks * SLAB, SLAB, 128),
+                        umma_desc(wb_u + 2 * ks * 512, 512, 128), tc_idesc(32), ks > 0 ? 1u : 0u);
+          umma_commit(&tfull[buf]);
+          umma_commit(&empty[s]);  // one of the slot's two arrivals
+        }
+      }
+      umma_commit(done);
+      tc_drain(done, 0);
+    }
+    __syncwarp();
+  } else {
+    // ---- math warps ----
+    const int mt = tid - 64;                         // 0 .. 255
+    const int t_out = mt >> 7, i_out = mt & 127;     // this thread's output cell in the tile
+    const int q4 = warp & 3, m = 32 * q4 + lane;     // TMEM lane = tile cell
+    const int L0 = warp < 6 ? 0 : 2;                 // this warp's two lines of D
+    const float bias = a.bias[0];
+    long long g = 0;
+    bool ok = true;
+    for (long long u = blockIdx.x; u < a.nunits && ok; u += gridDim.x) {
+      const TcUnit p = tc_unit(a.g, a.nchunk, TC_CHUNK, u);
+      float acc_prev = 0.0f, acc_cur = 0.0f, acc_next = 0.0f;  // outputs k - 1, k, k + 1
+      for (int k = p.k0 - 1; k <= p.k1; k++, g++) {
+        const int s = (int)(g % TO_RING), buf = (int)(g % TO_NBUF);
+        float *ds = ds0 + (g & 1) * TO_DS_FLOATS;
+        bool w = tc_wait(&tfull[buf], (uint32_t)((g / TO_NBUF) & 1), abort_s);
+        w = __all_sync(0xffffffffu, w);
+        if (w) {
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          uint32_t r[2][32];
+#pragma unroll
+          for (int h = 0; h < 2; h++) tmem_ld32(tmem + ((uint32_t)(32 * q4) << 16) + buf * 128 + (L0 + h) * 32, r[h]);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) tc_arrive(&tempty[buf]);
+#pragma unroll
+          for (int h = 0; h < 2; h++)
+#pragma unroll
+            for (int tap = 0; tap < NTAP; tap++)
+              ds[((L0 + h) * NTAP + tap) * TC_ROWS + 1 + m] = __uint_as_float(r[h][tap]);
+        }
+        if (w && mt < 8 * NTAP) {  // D of the r-halo cells (rows 0 and 129 of each line)
+          const int hc = mt / NTAP, tap = mt - hc * NTAP, L = hc >> 1, row = (hc & 1) ? TC_ROWS - 1 : 0;
+          w = tc_wait(&full[s], (uint32_t)((g / TO_RING) & 1), abort_s);
+          float dsum = 0.0f;
+          if (w) {
+            const unsigned char *src = ring + s * PB + (L * TC_ROWS + row) * 16;
+#pragma unroll
+            for (int slab = 0; slab < 4; slab++) {
+              const uint4 v = *reinterpret_cast<const uint4 *>(src + slab * SLAB);
+              const __nv_bfloat16 *x = reinterpret_cast<const __nv_bfloat16 *>(&v);
+#pragma unroll
+              for (int c = 0; c < 8; c++)
+                dsum = fmaf(__bfloat162float(x[c]), __bfloat162float(a.w[(slab * 8 + c) * NTAP + tap]), dsum);
+            }
+          }
+          ds[(L * NTAP + tap) * TC_ROWS + row] = dsum;
+        }
+        if (!math_bar_and(w)) {  // ds complete, slot s no longer read by the math warps
+          ok = false;
+          break;
+        }
+        if (mt == 0) tc_arrive(&empty[s]);
+        // contributions of input plane k: tap (dr, dt, dp) takes D at (i + dr, j + dt) of the
+        // plane k = output plane + dp
+        float c[3];
+#pragma unroll
+        for (int dp = 0; dp < 3; dp++) {
+          float sum = 0.0f;
+#pragma unroll
+          for (int dt = 0; dt < 3; dt++)
+#pragma unroll
+            for (int dr = 0; dr < 3; dr++)
+              sum += ds[((t_out + dt) * NTAP + dp * 9 + dt * 3 + dr) * TC_ROWS + i_out + dr];
+          c[dp] = sum;
+        }
+        acc_prev += c[2];  // output k - 1 (dp = +1): complete now
+        acc_cur += c[1];
+        acc_next += c[0];
+        const int ko = k - 1;
+        if (ko >= p.k0 && ko < p.k1 && p.j0 + t_out < a.g.nth)
+          a.y[(long long)p.b * a.g.nc + ((long long)ko * a.g.nth + p.j0 + t_out) * a.g.nr + p.i0 + i_out] =
+              bias + acc_prev;
+        acc_prev = acc_cur;
+        acc_cur = acc_next;
+        acc_next = 0.0f;
+      }
+    }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (tid == 0 && *abort_s) atomicOr(a.kerr, 1);
-  if (warp == 0) {
+  if (warp == 1) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TO_TMEM_COLS));
   }
@@ -911,6 +941,7 @@ struct WgArgs {
   const __nv_bfloat16 *dout;  // [cells][COUT] gradient at the layer's output
   float *part;                // [gridDim.x][27][COUT][CIN]
   float *partb;               // [gridDim.x][COUT]
+  long long ss;               // slab stride of in and dout (0: channels-last)
 };
 
 template <int CIN, int COUT>
@@ -947,8 +978,8 @@ __global__ void __launch_bounds__(WG_THREADS, 1) k_wgrad(WgArgs a) {
 
   for (long long id = blockIdx.x; id < a.g.nbricks; id += gridDim.x) {
     const BrickPos p = brick_pos(a.g, id);
-    stage_halo<CIN>(a.g, p, a.in, halo);
-    stage_brick<COUT>(a.g, p, a.dout, dsm);
+    stage_halo<CIN>(a.g, p, a.in, halo, a.ss);
+    stage_brick<COUT>(a.g, p, a.dout, dsm, a.ss);
     cp_async_wait_all();
     __syncthreads();
 #pragma unroll 1
@@ -1089,32 +1120,37 @@ __global__ void __launch_bounds__(EW) k_to_bf16(int n, const float *__restrict__
   if (q < n) b[q] = __float2bfloat16_rn(a[q]);
 }
 
-// FP32 channel-major [5][cells] -> BF16 [cells][16]
+// 16 BF16 channels of one cell into a 16-channel activation (layout as chunk_ptr)
+__device__ __forceinline__ void store16(__nv_bfloat16 *out, long long c, long long ss, const __nv_bfloat16 (&v)[16]) {
+  uint4 *d0 = reinterpret_cast<uint4 *>(ss ? out + c * 8 : out + c * 16);
+  uint4 *d1 = reinterpret_cast<uint4 *>(ss ? out + ss + c * 8 : out + c * 16 + 8);
+  *d0 = reinterpret_cast<const uint4 *>(v)[0];
+  *d1 = reinterpret_cast<const uint4 *>(v)[1];
+}
+
+// FP32 channel-major [5][cells] -> 16-channel BF16 activation (slab stride ss, 0: channels-last)
 __global__ void __launch_bounds__(EW) k_pack_input(long long cells, const float *__restrict__ in,
-                                                   __nv_bfloat16 *__restrict__ out) {
+                                                   __nv_bfloat16 *__restrict__ out, long long ss) {
   const long long c = (long long)blockIdx.x * EW + threadIdx.x;
   if (c >= cells) return;
   __align__(16) __nv_bfloat16 v[16];
 #pragma unroll
   for (int ch = 0; ch < 16; ch++) v[ch] = __float2bfloat16_rn(ch < 5 ? in[ch * cells + c] : 0.0f);
-  uint4 *dst = reinterpret_cast<uint4 *>(out + c * 16);
-  dst[0] = reinterpret_cast<uint4 *>(v)[0];
-  dst[1] = reinterpret_cast<uint4 *>(v)[1];
+  store16(out, c, ss, v);
 }
 
 // features of one grid straight into the packed layout: (T - 1e6)/1e6, bhat, log10 dt
 __global__ void __launch_bounds__(EW) k_features(long long N, const double *__restrict__ T,
                                                  const double *__restrict__ bhat, float logdt,
-                                                 __nv_bfloat16 *__restrict__ out, float *__restrict__ f32) {
+                                                 __nv_bfloat16 *__restrict__ out, float *__restrict__ f32,
+                                                 long long ss) {
   const long long c = (long long)blockIdx.x * EW + threadIdx.x;
   if (c >= N) return;
   float f[5] = {(float)((T[c] - 1e6) * 1e-6), (float)bhat[c], (float)bhat[N + c], (float)bhat[2 * N + c], logdt};
   __align__(16) __nv_bfloat16 v[16];
 #pragma unroll
   for (int ch = 0; ch < 16; ch++) v[ch] = __float2bfloat16_rn(ch < 5 ? f[ch] : 0.0f);
-  uint4 *dst = reinterpret_cast<uint4 *>(out + c * 16);
-  dst[0] = reinterpret_cast<uint4 *>(v)[0];
-  dst[1] = reinterpret_cast<uint4 *>(v)[1];
+  store16(out, c, ss, v);
   if (f32) {
 #pragma unroll
     for (int ch = 0; ch < 5; ch++) f32[ch * N + c] = f[ch];
@@ -1139,7 +1175,8 @@ __global__ void __launch_bounds__(EW) k_sum(long long n, const float *__restrict
 // dy = 2 w (y - t) / sum w into channel 0 of a 16-channel BF16 tensor; partial sums of w e^2
 __global__ void __launch_bounds__(EW) k_loss(long long n, const float *__restrict__ y, const float *__restrict__ t,
                                              const float *__restrict__ w, const double *__restrict__ wpart,
-                                             int nwpart, __nv_bfloat16 *__restrict__ dy, double *__restrict__ part) {
+                                             int nwpart, __nv_bfloat16 *__restrict__ dy, double *__restrict__ part,
+                                             long long ss) {
   __shared__ double red[EW];
   __shared__ float scale_s;
   if (threadIdx.x == 0) {
@@ -1157,9 +1194,7 @@ __global__ void __launch_bounds__(EW) k_loss(long long n, const float *__restric
     v[0] = __float2bfloat16_rn(scale * wq * e);
 #pragma unroll
     for (int ch = 1; ch < 16; ch++) v[ch] = __float2bfloat16_rn(0.0f);
-    uint4 *dst = reinterpret_cast<uint4 *>(dy + q * 16);
-    dst[0] = reinterpret_cast<uint4 *>(v)[0];
-    dst[1] = reinterpret_cast<uint4 *>(v)[1];
+    store16(dy, q, ss, v);
     s += (double)wq * (double)e * (double)e;
   }
   red[threadIdx.x] = s;
@@ -1354,9 +1389,9 @@ TmapEncodeFn tmap_encoder() {
   return fn;
 }
 
-// tensor map of a [cells][cin] BF16 activation viewed as {8 channels, r, theta, cin / 8 slabs,
-// box * phi}, box {8, 130, 4, cin / 8, 1}: a box lands in shared memory as
-// [slab][line][r][8 channels]
+// tensor map of a planar [cin / 8][cells][8] BF16 activation viewed as {8 channels, r, theta,
+// cin / 8 slabs, box * phi}, box {8, 130, 4, cin / 8, 1}: a box lands in shared memory as
+// [slab][line][r][8 channels], and each line of a slab is one contiguous run of 130 x 16 bytes
 int tc_tmap(rkl_ws *ws, const Boxes &g, const __nv_bfloat16 *in, int cin, CUtensorMap *map) {
   const TmapEncodeFn enc = tmap_encoder();
   if (!enc) {
@@ -1365,8 +1400,8 @@ int tc_tmap(rkl_ws *ws, const Boxes &g, const __nv_bfloat16 *in, int cin, CUtens
   }
   const cuuint64_t dims[5] = {8, (cuuint64_t)g.nr, (cuuint64_t)g.nth, (cuuint64_t)(cin / 8),
                               (cuuint64_t)g.nbox * (cuuint64_t)g.nph};
-  const cuuint64_t strides[4] = {(cuuint64_t)cin * 2, (cuuint64_t)g.nr * cin * 2, 16,
-                                 (cuuint64_t)g.nth * g.nr * cin * 2};
+  const cuuint64_t strides[4] = {16, (cuuint64_t)g.nr * 16, (cuuint64_t)(g.nc * g.nbox) * 16,
+                                 (cuuint64_t)g.nth * g.nr * 16};
   const cuuint32_t box[5] = {8, (cuuint32_t)TC_ROWS, (cuuint32_t)TC_LINES, (cuuint32_t)(cin / 8), 1};
   const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
   const CUresult cr = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<__nv_bfloat16 *>(in), dims, strides,
@@ -1390,6 +1425,7 @@ int launch_conv_tc(rkl_ws *ws, const Boxes &g, const __nv_bfloat16 *in, const __
   a.bias = bias;
   a.mask = mask;
   a.out = out;
+  a.ss = 8 * g.nc * g.nbox;
   a.nchunk = (g.nph + TC_C - 1) / TC_C;
   a.nunits = (long long)g.nbox * (g.nr / TC_R) * ((g.nth + TC_T - 1) / TC_T) * a.nchunk;
   a.kerr = ws->kerr;
@@ -1412,7 +1448,7 @@ int launch_conv_out_tc(rkl_ws *ws, const Boxes &g, const __nv_bfloat16 *in, cons
   a.nunits = (long long)g.nbox * (g.nr / TC_R) * ((g.nth + TC_T - 1) / TC_T) * a.nchunk;
   a.kerr = ws->kerr;
   const long long grid = a.nunits < ws->nsm ? a.nunits : ws->nsm;
-  k_conv_out_tc<<<(unsigned)grid, TC_THREADS, to_smem_bytes(), ws->stream>>>(map, a);
+  k_conv_out_tc<<<(unsigned)grid, TO_THREADS, to_smem_bytes(), ws->stream>>>(map, a);
   ws->launches += 1;
   return RKL_OK;
 }
@@ -1431,12 +1467,13 @@ void launch_conv(rkl_ws *ws, const Boxes &g, const __nv_bfloat16 *in, const uint
 }
 
 template <int CIN, int COUT>
-int launch_wgrad(rkl_ws *ws, const Boxes &g, const __nv_bfloat16 *in, const __nv_bfloat16 *dout, int l) {
+int launch_wgrad(rkl_ws *ws, const Boxes &g, const __nv_bfloat16 *in, const __nv_bfloat16 *dout, int l,
+                 long long ss) {
   const int nblk = (int)(g.nbricks < ws->nsm ? g.nbricks : ws->nsm);
   const size_t need = (size_t)nblk * (NTAP * COUT * CIN + COUT);
   int rc = ensure_part(ws, need);
   if (rc) return rc;
-  WgArgs a{g, in, dout, ws->part, ws->part + (size_t)nblk * NTAP * COUT * CIN};
+  WgArgs a{g, in, dout, ws->part, ws->part + (size_t)nblk * NTAP * COUT * CIN, ss};
   k_wgrad<CIN, COUT><<<nblk, WG_THREADS, wgrad_smem_bytes<CIN, COUT>(), ws->stream>>>(a);
   const int nout = L_COUT[l] * L_CIN[l] * NTAP + L_COUT[l];
   k_wgrad_reduce<<<(nout + EW - 1) / EW, EW, 0, ws->stream>>>(nblk, CIN, COUT, L_CIN[l], L_COUT[l], a.part, a.partb,
@@ -1634,7 +1671,8 @@ int ws_forward(rkl_ws *ws, const int box[3], int nbox, int periodic_phi, const f
   Bufs b;
   int rc = carve(ws, cells, false, b);
   if (rc) return rc;
-  k_pack_input<<<(unsigned)((cells + EW - 1) / EW), EW, 0, ws->stream>>>(cells, in, b.a0);
+  k_pack_input<<<(unsigned)((cells + EW - 1) / EW), EW, 0, ws->stream>>>(cells, in, b.a0,
+                                                                       tc_applies(g) ? 8 * cells : 0);
   ws->launches += 1;
   Bufs o = b;
   o.y = out;
@@ -1651,35 +1689,36 @@ int ws_loss_grad(rkl_ws *ws, const int box[3], int nbox, int periodic_phi, const
   int rc = carve(ws, cells, true, b);
   if (rc) return rc;
   const unsigned eg = (unsigned)((cells + EW - 1) / EW);
-  k_pack_input<<<eg, EW, 0, ws->stream>>>(cells, in, b.a0);
+  const long long ss = tc_applies(g) ? 8 * cells : 0;  // planar activations on the tcgen05 path
+  k_pack_input<<<eg, EW, 0, ws->stream>>>(cells, in, b.a0, ss);
   if ((rc = run_forward(ws, g, b))) return rc;
   k_sum<<<RED_BLOCKS, EW, 0, ws->stream>>>(cells, weight, ws->red);
   k_loss<<<RED_BLOCKS, EW, 0, ws->stream>>>(cells, b.y, target, weight, ws->red, RED_BLOCKS, b.dy,
-                                            ws->red + RED_BLOCKS);
+                                            ws->red + RED_BLOCKS, ss);
   ws->launches += 3;
   // layer 4: dW4 from (dy, a3); dz3 = W4^T dy masked by a3 > 0
-  if ((rc = launch_wgrad<32, 16>(ws, g, b.a3, b.dy, 3))) return rc;
+  if ((rc = launch_wgrad<32, 16>(ws, g, b.a3, b.dy, 3, ss))) return rc;
   if (tc_applies(g)) {
     if ((rc = launch_conv_tc<16, EPI_MASK>(ws, g, b.dy, ws->wuma[3], nullptr, b.a3, b.dzA))) return rc;
   } else {
     launch_conv<16, 4, EPI_MASK>(ws, g, b.dy, ws->wadj[3], nullptr, b.a3, b.dzA);
   }
   // layer 3: dW3 from (dz3, a2); dz2 = W3^T dz3 masked by a2 > 0
-  if ((rc = launch_wgrad<32, 32>(ws, g, b.a2, b.dzA, 2))) return rc;
+  if ((rc = launch_wgrad<32, 32>(ws, g, b.a2, b.dzA, 2, ss))) return rc;
   if (tc_applies(g)) {
     if ((rc = launch_conv_tc<32, EPI_MASK>(ws, g, b.dzA, ws->wuma[2], nullptr, b.a2, b.dzB))) return rc;
   } else {
     launch_conv<32, 4, EPI_MASK>(ws, g, b.dzA, ws->wadj[2], nullptr, b.a2, b.dzB);
   }
   // layer 2: dW2 from (dz2, a1); dz1 = W2^T dz2 masked by a1 > 0
-  if ((rc = launch_wgrad<32, 32>(ws, g, b.a1, b.dzB, 1))) return rc;
+  if ((rc = launch_wgrad<32, 32>(ws, g, b.a1, b.dzB, 1, ss))) return rc;
   if (tc_applies(g)) {
     if ((rc = launch_conv_tc<32, EPI_MASK>(ws, g, b.dzB, ws->wuma[1], nullptr, b.a1, b.dzA))) return rc;
   } else {
     launch_conv<32, 4, EPI_MASK>(ws, g, b.dzB, ws->wadj[1], nullptr, b.a1, b.dzA);
   }
   // layer 1: dW1 from (dz1, a0)
-  if ((rc = launch_wgrad<16, 32>(ws, g, b.a0, b.dzA, 0))) return rc;
+  if ((rc = launch_wgrad<16, 32>(ws, g, b.a0, b.dzA, 0, ss))) return rc;
   if ((rc = ws_cuda(ws, cudaGetLastError()))) return rc;
   if (loss_out) {
     std::vector<double> h(2 * RED_BLOCKS);
@@ -1718,7 +1757,8 @@ int ws_features(rkl_ws *ws, const rkl_grid *grid, const double *T, const double 
   Bufs b;
   int rc = carve(ws, N, false, b);
   if (rc) return rc;
-  k_features<<<(unsigned)((N + EW - 1) / EW), EW, 0, ws->stream>>>(N, T, bhat, (float)std::log10(dt), b.a0, feat);
+  k_features<<<(unsigned)((N + EW - 1) / EW), EW, 0, ws->stream>>>(N, T, bhat, (float)std::log10(dt), b.a0, feat,
+                                                                   0);
   ws->launches += 1;
   return ws_cuda(ws, cudaGetLastError());
 }
@@ -1734,7 +1774,7 @@ int ws_guess(rkl_ws *ws, const rkl_grid *grid, const double *T, const double *bh
   int rc = carve(ws, N, false, b);
   if (rc) return rc;
   const unsigned eg = (unsigned)((N + EW - 1) / EW);
-  k_features<<<eg, EW, 0, ws->stream>>>(N, T, bhat, (float)std::log10(dt), b.a0, nullptr);
+  k_features<<<eg, EW, 0, ws->stream>>>(N, T, bhat, (float)std::log10(dt), b.a0, nullptr, tc_applies(g) ? 8 * N : 0);
   if ((rc = run_forward(ws, g, b))) return rc;
   k_guess<<<eg, EW, 0, ws->stream>>>(N, T, b.y, scale, x0);
   ws->launches += 2;
