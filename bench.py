@@ -97,6 +97,9 @@ def parse_args():
                                          "pcg-jacobi-mix", "pcg-bilu0-mix", "ws-forward", "ws-train",
                                          "visc-stage", "visc-pcg-jacobi", "visc-pcg-bilu0"),
                    help="run only a minimal case of one kernel family for an ncu capture (no timing)")
+    p.add_argument("--profile-grid", type=int, nargs=3, metavar=("NR", "NTH", "NPH"), default=list(GRID),
+                   help="grid of the --profile case (default the bench grid); a smaller grid keeps an ncu "
+                        "capture of many passes small")
     p.add_argument("--plain-launches", action="store_true",
                    help="run every step with the library's event profiler on (plain launches, no graphs), so "
                         "that an ncu launch list sees every kernel; not a bench number")
@@ -804,7 +807,7 @@ def profile_case(args):
     from paper_1610_01265_gb300 import synth
 
     B.build()
-    nr, nth, nph = GRID
+    nr, nth, nph = args.profile_grid
     c = synth.conduction_case(nr, nth, nph, args.seed)
     dev = lambda a: torch.from_numpy(np.array(a, dtype=np.float64)).cuda().view(-1)  # noqa: E731
     T, b, n = dev(c["T"]), dev(c["bhat"]), dev(c["n"])
