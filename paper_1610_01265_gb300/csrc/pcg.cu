@@ -29,9 +29,9 @@ namespace {
 constexpr int RB = 256;   // block size of grid-stride reduction kernels
 constexpr int NSL = 19;   // slots of an ILU row: 0 diag, 1+m = -FWD[m], 10+m = +FWD[m]
 
-__device__ __forceinline__ int slot_di(int s) { return s == 0 ? 0 : (s < 10 ? -fwd_di(s - 1) : fwd_di(s - 10)); }
-__device__ __forceinline__ int slot_dj(int s) { return s == 0 ? 0 : (s < 10 ? -fwd_dj(s - 1) : fwd_dj(s - 10)); }
-__device__ __forceinline__ int slot_dk(int s) { return s == 0 ? 0 : (s < 10 ? -fwd_dk(s - 1) : fwd_dk(s - 10)); }
+__host__ __device__ constexpr int slot_di(int s) { return s == 0 ? 0 : (s < 10 ? -fwd_di(s - 1) : fwd_di(s - 10)); }
+__host__ __device__ constexpr int slot_dj(int s) { return s == 0 ? 0 : (s < 10 ? -fwd_dj(s - 1) : fwd_dj(s - 10)); }
+__host__ __device__ constexpr int slot_dk(int s) { return s == 0 ? 0 : (s < 10 ? -fwd_dk(s - 1) : fwd_dk(s - 10)); }
 
 // Sum NV per-thread values over the whole grid.  Returns true (in every thread of the
 // last block to finish) with the totals in tot[] of thread 0.  Blocks must be 1-D with a
@@ -545,11 +545,11 @@ __device__ __forceinline__ int slot_ldelta(const IluPlan &pl, int s) {
   return slot_di(s) + pl.bi * (slot_dj(s) + pl.bj * slot_dk(s));
 }
 
-__device__ __forceinline__ int lex_rank(int s) {
+__host__ __device__ constexpr int lex_rank(int s) {
   return (slot_dk(s) + 1) * 9 + (slot_dj(s) + 1) * 3 + (slot_di(s) + 1);
 }
 
-__device__ __forceinline__ int slot_of_offset(int di, int dj, int dk) {
+__host__ __device__ constexpr int slot_of_offset(int di, int dj, int dk) {
   if (di == 0 && dj == 0 && dk == 0) return 0;
   for (int m = 0; m < 9; m++) {
     if (fwd_di(m) == di && fwd_dj(m) == dj && fwd_dk(m) == dk) return 10 + m;
@@ -587,36 +587,61 @@ __global__ void __launch_bounds__(GB) k_bilu_factor(Dims d, IluPlan pl,
       const int bb = q / nl, l = pl.lev_cell[ls + (q - bb * nl)];
       const size_t p = (size_t)pl.G * ls + q;
       BlockCell b = block_cell(d, pl, b0 + bb, l);
+      int mask = 0;  // bit s: slot s inside the block and the pattern
+#pragma unroll
+      for (int q2 = 0; q2 < NSL; q2++)
+        if (in_pattern<OP>(pl, b, q2)) mask |= 1 << q2;
       double a[NSL];
       a[0] = fma(dt, S_diag<OP>(d, coef, b.c), W[b.c]);
+#pragma unroll
       for (int m = 0; m < 9; m++) {
         a[1 + m] = 0.0;
         a[10 + m] = 0.0;
         if (m >= nf) continue;
-        long long off = fwd_di(m) + (long long)fwd_dj(m) * d.nr + (long long)fwd_dk(m) * d.nrt;
-        if (in_pattern<OP>(pl, b, 10 + m)) a[10 + m] = dt * coef[m * d.N + b.c];
-        if (in_pattern<OP>(pl, b, 1 + m))  // full rows keep the backward entries themselves
+        const long long off = fwd_di(m) + (long long)fwd_dj(m) * d.nr + (long long)fwd_dk(m) * d.nrt;
+        if (mask & (1 << (10 + m))) a[10 + m] = dt * coef[m * d.N + b.c];
+        if (mask & (1 << (1 + m)))  // full rows keep the backward entries themselves
           a[1 + m] = dt * (OP == OPK_FLUX ? coef[(10 + m) * d.N + b.c] : coef[m * d.N + b.c - off]);
       }
-      // lower slots in increasing order of the neighbour's position (lexicographic)
+      // lower slots in increasing order of the neighbour's position (lexicographic); the
+      // slot arithmetic is resolved at compile time, only the pattern mask is tested here
+#pragma unroll
       for (int rk = 0; rk < 13; rk++) {
-        int s = -1;
-        for (int q2 = 1; q2 < 10; q2++)
-          if (lex_rank(q2) == rk) s = q2;
-        if (s < 0 || !in_pattern<OP>(pl, b, s)) continue;
-        const int kp = group_pos(pl, bb, l + slot_ldelta(pl, s));
-        const double L = a[s] / LUg[kp];  // U_kk, slot 0
-        a[s] = L;
-        for (int q2 = 0; q2 < NSL; q2++) {
-          if (lex_rank(q2) <= rk || !in_pattern<OP>(pl, b, q2)) continue;
-          int s3 = slot_of_offset(slot_di(q2) - slot_di(s), slot_dj(q2) - slot_dj(s),
-                                  slot_dk(q2) - slot_dk(s));
-          if (s3 < 0 || lu_slot(PAT, s3) < 0) continue;
-          a[q2] -= L * LUg[(size_t)lu_slot(PAT, s3) * gs + kp];
+#pragma unroll
+        for (int s = 1; s < 10; s++) {
+          if (lex_rank(s) != rk) continue;
+          // the loads do not depend on a[], so they are issued unconditionally (a slot outside
+          // the pattern reads the row's own, valid position and the values are not used) and
+          // the compiler can start them ahead of the eliminations before them
+          const bool has = mask & (1 << s);
+          const size_t kp = has ? (size_t)group_pos(pl, bb, l + slot_ldelta(pl, s)) : p;
+          const double ukk = LUg[kp];  // U_kk, slot 0
+          double u[NSL];
+#pragma unroll
+          for (int q2 = 0; q2 < NSL; q2++) {
+            u[q2] = 0.0;
+            if (lex_rank(q2) <= rk) continue;
+            const int s3 = slot_of_offset(slot_di(q2) - slot_di(s), slot_dj(q2) - slot_dj(s),
+                                          slot_dk(q2) - slot_dk(s));
+            if (s3 < 0 || lu_slot(PAT, s3) < 0) continue;
+            u[q2] = LUg[(size_t)lu_slot(PAT, s3) * gs + kp];
+          }
+          if (!has) continue;
+          const double L = a[s] / ukk;
+          a[s] = L;
+#pragma unroll
+          for (int q2 = 0; q2 < NSL; q2++) {
+            if (lex_rank(q2) <= rk) continue;
+            const int s3 = slot_of_offset(slot_di(q2) - slot_di(s), slot_dj(q2) - slot_dj(s),
+                                          slot_dk(q2) - slot_dk(s));
+            if (s3 < 0 || lu_slot(PAT, s3) < 0 || !(mask & (1 << q2))) continue;
+            a[q2] -= L * u[q2];
+          }
         }
       }
+#pragma unroll
       for (int q2 = 0; q2 < NSL; q2++)
-        if (lu_slot(PAT, q2) >= 0) LUg[(size_t)lu_slot(PAT, q2) * gs + p] = in_pattern<OP>(pl, b, q2) ? a[q2] : 0.0;
+        if (lu_slot(PAT, q2) >= 0) LUg[(size_t)lu_slot(PAT, q2) * gs + p] = (mask & (1 << q2)) ? a[q2] : 0.0;
       LUg[(size_t)lu_slot(PAT, 19) * gs + p] = 1.0 / a[0];
     }
     __syncthreads();
