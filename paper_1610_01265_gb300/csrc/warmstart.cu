@@ -712,7 +712,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(const __grid_constant
 //              leave together if one wait gives up), the 27-tap sums and the y stores.
 constexpr int TO_RING = 3, TO_NBUF = 4, TO_TMEM_COLS = 512, TO_THREADS = 320;
 constexpr int TO_DS_FLOATS = TC_LINES * NTAP * TC_ROWS;  // D of one plane, [line][tap][130 cells]
-constexpr int to_smem_bytes() { return TO_RING * tc_plane_bytes<32>() + 2 * TO_DS_FLOATS * 4 + 2048 + 512; }
+constexpr int to_smem_bytes() { return TO_RING * tc_plane_bytes<32>() + 2 * TO_DS_FLOATS * 4 + 2048 + NTAP * 32 * 4 + 512; }
 
 struct ToArgs {
   Boxes g;
@@ -742,7 +742,8 @@ __global__ void __launch_bounds__(TO_THREADS, 1) k_conv_out_tc(const __grid_cons
   unsigned char *ring = smem;                                      // TO_RING staged planes
   float *ds0 = reinterpret_cast<float *>(ring + TO_RING * PB);     // 2 x [4][27][130]
   __nv_bfloat16 *wb = reinterpret_cast<__nv_bfloat16 *>(ds0 + 2 * TO_DS_FLOATS);  // B: [4 slabs][32 taps][8 ci]
-  uint64_t *full = reinterpret_cast<uint64_t *>(wb + 1024);        // [TO_RING]
+  float *wf = reinterpret_cast<float *>(wb + 1024);                // [27 taps][32 ci], FP32, for the r halo
+  uint64_t *full = reinterpret_cast<uint64_t *>(wf + NTAP * 32);   // [TO_RING]
   uint64_t *empty = full + TO_RING;                                // [TO_RING]
   uint64_t *tfull = empty + TO_RING;                               // [TO_NBUF]
   uint64_t *tempty = tfull + TO_NBUF;                              // [TO_NBUF]
@@ -757,6 +758,7 @@ __global__ void __launch_bounds__(TO_THREADS, 1) k_conv_out_tc(const __grid_cons
     const int slab = q >> 8, n = (q >> 3) & 31, ci = slab * 8 + (q & 7);
     wb[q] = n < NTAP ? a.w[ci * NTAP + n] : __float2bfloat16(0.0f);
   }
+  for (int q = tid; q < NTAP * 32; q += TO_THREADS) wf[q] = __bfloat162float(a.w[(q & 31) * NTAP + (q >> 5)]);
   if (tid == 0) {
     for (int s = 0; s < TO_RING; s++) {
       tc_bar_init(&full[s], 1);
@@ -878,19 +880,22 @@ __global__ void __launch_bounds__(TO_THREADS, 1) k_conv_out_tc(const __grid_cons
             for (int tap = 0; tap < NTAP; tap++)
               ds[((L0 + h) * NTAP + tap) * TC_ROWS + 1 + m] = __uint_as_float(r[h][tap]);
         }
-        if (w && mt < 8 * NTAP) {  // D of the r-halo cells (rows 0 and 129 of each line)
+        // D of the r-halo cells (rows 0 and 129 of each line); outside the box (the ends of
+        // the r range) the staged rows are zero and so is D, written without the products
+        if (w && mt < 8 * NTAP) {
           const int hc = mt / NTAP, tap = mt - hc * NTAP, L = hc >> 1, row = (hc & 1) ? TC_ROWS - 1 : 0;
-          w = tc_wait(&full[s], (uint32_t)((g / TO_RING) & 1), abort_s);
+          const bool inside = row == 0 ? p.i0 > 0 : p.i0 + TC_R < a.g.nr;
           float dsum = 0.0f;
-          if (w) {
+          if (inside) w = tc_wait(&full[s], (uint32_t)((g / TO_RING) & 1), abort_s);
+          if (inside && w) {
             const unsigned char *src = ring + s * PB + (L * TC_ROWS + row) * 16;
+            const float *wt = wf + tap * 32;
 #pragma unroll
             for (int slab = 0; slab < 4; slab++) {
               const uint4 v = *reinterpret_cast<const uint4 *>(src + slab * SLAB);
               const __nv_bfloat16 *x = reinterpret_cast<const __nv_bfloat16 *>(&v);
 #pragma unroll
-              for (int c = 0; c < 8; c++)
-                dsum = fmaf(__bfloat162float(x[c]), __bfloat162float(a.w[(slab * 8 + c) * NTAP + tap]), dsum);
+              for (int c = 0; c < 8; c++) dsum = fmaf(__bfloat162float(x[c]), wt[slab * 8 + c], dsum);
             }
           }
           ds[(L * NTAP + tap) * TC_ROWS + row] = dsum;
