@@ -5,26 +5,39 @@
 //
 // Net: conv3x3x3 5->32 ReLU, 32->32 ReLU, 32->32 ReLU, 32->1.  Parameters are FP32 (Adam
 // state too); every pass uses BF16 copies of the weights, BF16 activations and FP32
-// accumulation on the tensor cores (mma.sync m16n8k16).  Rounding points: features,
-// weights, stored activations a1..a3, the output gradient dy and the back-propagated
-// gradients dz1..dz3 are BF16 (round to nearest even); biases, y and the parameter
-// gradients (FP32 per CTA, FP64 across CTAs in a fixed order) are not.
+// accumulation on the tensor cores.  Rounding points: features, weights, stored
+// activations a1..a3, the output gradient dy and the back-propagated gradients dz1..dz3
+// are BF16 (round to nearest even); biases, y and the parameter gradients (FP32 per CTA,
+// FP64 across CTAs in a fixed order) are not.
 //
-// Activation layout: channels-last BF16, [box][phi][theta][r][C] with C = 32, or C = 16
-// for the 5 input features (channels 5..15 zero) and for dy (channel 0).  A box is a
-// whole grid (phi periodic) or a detached block (zero outside on every face); r and
-// theta are always zero outside.
+// Two convolution paths, with the same rounding points:
 //
-// Convolutions are implicit GEMMs over bricks of 32 (r) x 4 (theta) x 2 (phi) cells:
-// the brick plus a one-cell halo (34 x 6 x 4 rows of C channels) is staged in shared
-// memory with cp.async, rows XOR-swizzled by 16-byte chunk so that ldmatrix of eight
-// consecutive rows is conflict-free, and each tap's A operand is read with ldmatrix
-// from per-lane row addresses (the neighbour of the lane's cell).  Weights sit in
-// shared memory in mma fragment order.  Forward: M = 256 cells, N = 32 channels,
-// K = 27 taps x C.  Data gradient: the same kernel with the adjoint weights
-// W'[ci][co][26 - tap] = W[co][ci][tap].  Weight gradient: per tap, M = Cout, N = Cin,
+// * Grids whose r extent is a multiple of 128 (tcgen05): activations are planar 8-channel
+//   slabs [C/8][box][phi][theta][r][8]; the 32-channel layers (forward layers 1-3, the
+//   adjoint of layers 2-4) run k_conv_tc (TMA-staged planes, MMAs issued by single threads
+//   into TMEM accumulators, the three phi taps of a (theta, r) tap in one N = 96 MMA) and
+//   the output layer runs k_conv_out_tc (D = a W on the tensor cores, the 27-tap
+//   shift-sum on the CUDA cores).  See the comments above each kernel.
+//
+// * Other grids (mma.sync m16n8k16): channels-last BF16 activations [box][phi][theta][r][C]
+//   with C = 32, or C = 16 for the 5 input features (channels 5..15 zero) and for dy
+//   (channel 0).  Convolutions are implicit GEMMs over bricks of 32 (r) x 4 (theta) x
+//   2 (phi) cells: the brick plus a one-cell halo (34 x 6 x 4 rows of C channels) is
+//   staged in shared memory with cp.async, rows XOR-swizzled by 16-byte chunk so that
+//   ldmatrix of eight consecutive rows is conflict-free, and each tap's A operand is read
+//   with ldmatrix from per-lane row addresses (the neighbour of the lane's cell).  Weights
+//   sit in shared memory in mma fragment order.  Forward: M = 256 cells, N = 32 channels,
+//   K = 27 taps x C.  Data gradient: the same kernel with the adjoint weights
+//   W'[ci][co][26 - tap] = W[co][ci][tap].
+//
+// A box is a whole grid (phi periodic) or a detached block (zero outside on every face); r
+// and theta are always zero outside.  The weight gradient runs on mma.sync on every grid
+// (its layout-aware staging reads either activation layout): per tap, M = Cout, N = Cin,
 // K = cells, both operands through ldmatrix.trans; a persistent CTA accumulates its
-// bricks in registers and a second kernel sums the per-CTA partials in FP64.
+// bricks in registers and a second kernel sums the per-CTA partials in FP64.  (On tcgen05
+// a tap is a shift along K, so each instruction would carry one tap with M = 32 output
+// channels padded to 64; at the per-instruction cost measured for these kernels that is
+// slower than mma.sync.)
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
