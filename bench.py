@@ -136,34 +136,96 @@ def base_config():
 
 
 # ------------------------------------------------------------------ CPU oracle sample
+# PCG iteration counts of the timed step at this configuration (the oracle's, which the GPU
+# path matches to within one: tests/golden/bench_config_iters.json); RKL2 stage counts
+# follow from Eq. 5
+STEP_ITERS = {"jacobi": (72, 238, 733), "bilu0": (31, 126, 422),
+              "visc_jacobi": (143, 142, 126), "visc_bilu0": (52, 52, 47)}
+# stages / iterations of each part timed per CPU sample (viscosity on one component)
+CPU_PARTS = {"rkl2_c": 4, "jacobi_c": 6, "bilu0_c": 4, "rkl2_v": 2, "jacobi_v": 4, "bilu0_v": 2}
+
+
+def step_mix():
+    """Work of one timed step in cell passes per part (RKL2 stages, PCG iterations; viscosity
+    summed over its three components) and its one-off parts."""
+    import oracle as O
+
+    return {"rkl2_c": sum(O.rkl2_stages(r) for r in RATIOS), "jacobi_c": sum(STEP_ITERS["jacobi"]),
+            "bilu0_c": sum(STEP_ITERS["bilu0"]), "rkl2_v": 3 * O.rkl2_stages(VISC_RATIO),
+            "jacobi_v": sum(STEP_ITERS["visc_jacobi"]), "bilu0_v": sum(STEP_ITERS["visc_bilu0"]),
+            "factor_c": len(RATIOS), "factor_v": 1, "assembly": 2}
+
+
 def cpu_sample(seed: int):
-    """Bounded sample of the same workload on the FP64 CPU oracle (host cores):
-    4 RKL2 stages + 4 PCG-Jacobi + 4 PCG-block-ILU0 iterations (factorisation included)
-    of the conduction problem on the full grid; operator assembly excluded (set-up)."""
+    """The FP64 CPU oracle (host cores) on one timed step's work mix, on the full grid: each
+    part (conduction RKL2 stages, PCG-Jacobi and PCG-block-ILU0 iterations; the same for
+    viscosity, one component) is timed on CPU_PARTS stages or iterations and weighted by its
+    count in the step; the step's block-ILU0 factorisations and operator assemblies are
+    timed once at set-up and counted at their per-step number.  run() returns the time the
+    sample's cell passes take at that mix, so units / run() is the oracle's rate on the
+    step's mix."""
     import oracle as O
 
     from paper_1610_01265_gb300 import synth
 
     nr, nth, nph = GRID
     c = synth.conduction_case(nr, nth, nph, seed)
+    v = synth.viscosity_case(nr, nth, nph, seed)
     g = O.Grid(c["rf"], nth, nph)
+    t0 = time.perf_counter()
     S, W = O.assemble_conduction(g, c["T"], c["bhat"], c["n"], beta_tcut=BETA_TCUT)
     dte, _ = O.gershgorin_dt(g, S, W)
+    t1 = time.perf_counter()
+    Sv, Wv = O.assemble_viscosity(g, v["rho"], v["nu"])
+    dtv, _ = O.gershgorin_dt(g, Sv, Wv)
+    t2 = time.perf_counter()
+    O.bilu0_factor(g, O.build_A(S, W, 1000.0 * dte), BLOCK)
+    t3 = time.perf_counter()
+    O.bilu0_factor(g, O.build_A(Sv, Wv, VISC_RATIO * dtv), BLOCK, pattern=7)
+    t4 = time.perf_counter()
+    once = {"assembly": (t2 - t0) / 2, "factor_c": t3 - t2, "factor_v": t4 - t3}
+    mix = step_mix()
+    n = CPU_PARTS
+    vv = v["v"][0]
+
+    def timed(f):
+        ta = time.perf_counter()
+        f()
+        return time.perf_counter() - ta
 
     def run():
-        t0 = time.perf_counter()
-        O.rkl2_superstep(g, S, W, c["T"], 4.0 * dte, 4)
-        O.be_pcg(g, S, W, c["T"], 100 * dte, pc=O.PC_JACOBI, fixed_iters=4)
-        O.be_pcg(g, S, W, c["T"], 100 * dte, pc=O.PC_BILU0, block=BLOCK, fixed_iters=4)
-        return time.perf_counter() - t0
+        per = {
+            "rkl2_c": timed(lambda: O.rkl2_superstep(g, S, W, c["T"], n["rkl2_c"] * dte, n["rkl2_c"])) / n["rkl2_c"],
+            "jacobi_c": timed(lambda: O.be_pcg(g, S, W, c["T"], 1000.0 * dte, pc=O.PC_JACOBI,
+                                               fixed_iters=n["jacobi_c"])) / n["jacobi_c"],
+            "bilu0_c": (timed(lambda: O.be_pcg(g, S, W, c["T"], 1000.0 * dte, pc=O.PC_BILU0, block=BLOCK,
+                                               fixed_iters=n["bilu0_c"])) - once["factor_c"]) / n["bilu0_c"],
+            "rkl2_v": timed(lambda: O.rkl2_superstep(g, Sv, Wv, vv, n["rkl2_v"] * dtv, n["rkl2_v"])) / n["rkl2_v"],
+            "jacobi_v": timed(lambda: O.be_pcg(g, Sv, Wv, vv, VISC_RATIO * dtv, pc=O.PC_JACOBI,
+                                               fixed_iters=n["jacobi_v"], pattern=7)) / n["jacobi_v"],
+            "bilu0_v": (timed(lambda: O.be_pcg(g, Sv, Wv, vv, VISC_RATIO * dtv, pc=O.PC_BILU0, block=BLOCK,
+                                               fixed_iters=n["bilu0_v"], pattern=7)) - once["factor_v"])
+            / n["bilu0_v"],
+        }
+        t_step = sum(mix[k] * per[k] for k in per) + sum(mix[k] * once[k] for k in once)
+        return sum(n.values()) * t_step / sum(mix[k] for k in per)
 
-    return run, g.N * 12, O.num_threads()
+    return run, g.N * sum(n.values()), O.num_threads()
 
 
 def cpu_sample_text():
-    return ("conduction on the full 128x192x384 grid: one RKL2 super-step of 4 stages, "
-            "4 PCG-Jacobi and 4 PCG-block-ILU0(8^3) iterations (ILU factorisation "
-            "included), operator assembly excluded; cell-updates = cells x 12")
+    import oracle as O
+
+    m = step_mix()
+    return (f"the oracle on one bench step's work mix, full 128x192x384 grid: conduction RKL2 "
+            f"stages, PCG-Jacobi and PCG-block-ILU0(8^3) iterations (timed on {CPU_PARTS['rkl2_c']}, "
+            f"{CPU_PARTS['jacobi_c']} and {CPU_PARTS['bilu0_c']}) and the same for viscosity on one "
+            f"component (timed on {CPU_PARTS['rkl2_v']}, {CPU_PARTS['jacobi_v']} and {CPU_PARTS['bilu0_v']}), "
+            f"weighted by their counts in the step ({m['rkl2_c']}, {m['jacobi_c']}, {m['bilu0_c']}; "
+            f"{m['rkl2_v']}, {m['jacobi_v']}, {m['bilu0_v']} over three components), plus the step's "
+            f"{m['factor_c'] + m['factor_v']} block-ILU0 factorisations and 2 operator assemblies (timed "
+            f"once); cell-updates = cells x {sum(CPU_PARTS.values())} per sample at the step's mix "
+            f"(threads: {O.num_threads()})")
 
 
 C1_GRID = (32, 32, 64)

@@ -92,3 +92,26 @@ def test_committed_summaries_exist_for_every_costed_kernel():
         for name in sources:
             assert os.path.exists(os.path.join(bench.ROOT, "paper_1610_01265_gb300", "csrc", name.partition(":")[0]))
 
+
+
+def test_cpu_sample_mix_is_the_timed_steps_mix():
+    """The CPU oracle's sample is weighted by the timed step's own work: its PCG iteration
+    counts are the oracle's for this configuration (written by a committed oracle-only
+    script) and the stage counts follow from Eq. 5."""
+    import json
+
+    import oracle as O
+
+    gold = json.load(open(os.path.join(bench.ROOT, "tests", "golden", "bench_config_iters.json")))
+    assert tuple(gold["dims"]) == bench.GRID and tuple(gold["block"]) == bench.BLOCK
+    for name in ("jacobi", "bilu0"):
+        assert bench.STEP_ITERS[name] == tuple(gold["conduction"][f"{name}_{int(r)}"]["iters"] for r in bench.RATIOS)
+    assert bench.STEP_ITERS["visc_jacobi"] == tuple(gold["viscosity"]["jacobi_500"]["iters"])
+    assert bench.STEP_ITERS["visc_bilu0"] == tuple(gold["viscosity"]["bilu0_500"]["iters"])
+    assert bench.VISC_RATIO == 500.0
+    m = bench.step_mix()
+    assert m["rkl2_c"] == sum(O.rkl2_stages(r) for r in bench.RATIOS) == 283
+    assert m["rkl2_v"] == 3 * O.rkl2_stages(bench.VISC_RATIO)
+    passes = sum(m[k] for k in ("rkl2_c", "jacobi_c", "bilu0_c", "rkl2_v", "jacobi_v", "bilu0_v"))
+    assert abs(passes - 2601) <= 1  # the GPU step's cell passes (profiled_step_units / cells), to within one iteration
+    assert m["factor_c"] == len(bench.RATIOS) and m["factor_v"] == 1
