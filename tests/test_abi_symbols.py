@@ -1,9 +1,12 @@
 """The C-ABI library builds for sm_103a, loads without a GPU and exports every function
-declared in include/*.h; the Python binding wraps exactly those names."""
+declared in include/*.h; the Python binding wraps exactly those names; without a GPU its
+constructors fail with RKL_ECUDA."""
 import ctypes
 import glob
 import os
 import re
+
+import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -50,3 +53,23 @@ def test_host_only_calls_without_gpu():
     from paper_1610_01265_gb300 import warmstart
 
     assert warmstart.num_params() == sum(co * ci * 27 + co for ci, co in warmstart.LAYERS) == 60577
+
+
+def test_no_gpu_fails_loudly():
+    """Without a CUDA device the library reports RKL_ECUDA from its constructors: there is no
+    CPU fallback behind the C ABI."""
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    from paper_1610_01265_gb300 import rklpcg as R
+    from paper_1610_01265_gb300 import synth
+    from paper_1610_01265_gb300 import warmstart as W
+
+    c = synth.conduction_case(8, 4, 8, 1)
+    with pytest.raises(R.RklError) as e:
+        R.Context(c["rf"], 4, 8)
+    assert e.value.code == R.RKL_ECUDA
+    with pytest.raises(R.RklError) as e:
+        W.Net(1)
+    assert e.value.code == R.RKL_ECUDA
